@@ -1,0 +1,221 @@
+/*
+ * qk.h -- C ABI of libqk, a GB300 (sm_103a) dense state-vector engine for the
+ * gate-application hot path of Quantum-Kit (Tankasala & Ilatikhameneh,
+ * arXiv:1908.07187).
+ *
+ * The calls follow the paper's command set (Q-Kit section): (1) add qubits,
+ * (2) perform a gate operation, (3) measure, (4) define a custom gate "as a
+ * matrix or as a function"; plus classical bits, copying a measured qubit into a
+ * classical bit and classically controlled gates (Q-Kit section; Appendix A
+ * commands AddCbits, Copy and "SigmaX 0,-k"), and viewing the state (Q-Kit
+ * section, Fig. 1b).
+ *
+ * State layout: one context holds one state of n qubits as 2^n complex
+ * amplitudes in device memory, interleaved (re, im), complex64 (2 x float) or
+ * complex128 (2 x double).  Logical qubit q is index bit q of the state as seen
+ * by qk_get_state / qk_set_state / qk_device_state.  Internally a SWAP only
+ * relabels qubits; the relabelling is undone before any state leaves the library.
+ *
+ * Register convention (Appendix A): in any target list the first-listed qubit is
+ * the most significant bit of the register value.
+ *
+ * Ownership: every input array is copied (or consumed) before the call returns;
+ * the context owns all device memory it allocates; outputs go into caller
+ * buffers.  Errors: every call returns a qk_status; nothing throws across the ABI.
+ * A call that fails argument checks leaves the context unchanged and sets the
+ * message returned by qk_last_error.  A QK_ECUDA status means a CUDA call failed;
+ * the context should then be destroyed.
+ *
+ * Ordering: gate, measure and cbit calls are enqueued on the context's CUDA
+ * stream and return without waiting, unless they have a host output
+ * (qk_measure with a non-NULL outcome, qk_read_cbits, qk_get_state, qk_sync).
+ * Measurement outcomes and classical conditions are evaluated on the device, so a
+ * classically controlled gate needs no host round trip.
+ *
+ * Thread safety: a context must not be used from two host threads at once.
+ */
+#ifndef QK_H
+#define QK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qk_ctx qk_ctx;
+
+typedef enum {
+    QK_OK = 0,
+    QK_EINVAL = -1,          /* bad argument (qubit out of range, duplicate, size) */
+    QK_ENOMEM = -2,          /* device or host allocation failed                   */
+    QK_EBUDGET = -3,         /* request exceeds the context's HBM budget           */
+    QK_ENOTBIJECTIVE = -4,   /* a function gate is not a permutation               */
+    QK_ENOTUNITARY = -5,     /* a matrix gate fails the unitarity tolerance        */
+    QK_ECUDA = -6,           /* a CUDA runtime call failed                         */
+    QK_ETIMEOUT = -7,        /* a device-side bounded wait gave up                 */
+    QK_ESTATE = -8           /* call not valid in the context's current state      */
+} qk_status;
+
+typedef enum { QK_C64 = 0, QK_C128 = 1 } qk_precision;
+
+/* Execution modes.  PLAIN: one kernel pass over the state per gate (the
+ * unfused baseline).  FUSED: gates are queued; at a flush point a planner groups
+ * runs of gates into shared-memory tile passes, so several gates cost one HBM
+ * read+write of the state. */
+typedef enum { QK_EXEC_PLAIN = 0, QK_EXEC_FUSED = 1 } qk_exec_mode;
+
+typedef struct {
+    int exec_mode;            /* qk_exec_mode; default QK_EXEC_FUSED                 */
+    int tile_qubits;          /* fused tile width m (qubits per tile); 0 = default   */
+    int max_pending;          /* queued ops that force a flush; 0 = default (4096)   */
+    int profile;              /* 1: time every launch with CUDA events (qk_profile)  */
+    size_t hbm_budget_bytes;  /* 0 = no limit beyond free device memory             */
+    int reserved[8];          /* must be zero                                         */
+} qk_options;
+
+/* Built-in gate ids for qk_apply_gate (negative; user gates get ids >= 0).
+ * Matrices are the textbook ones, row/column index = register value. */
+enum {
+    QK_GATE_X = -1,      /* SigmaX (Appendix A)                            */
+    QK_GATE_Y = -2,
+    QK_GATE_Z = -3,
+    QK_GATE_H = -4,      /* Hadamard (Appendix A)                          */
+    QK_GATE_S = -5,
+    QK_GATE_SDG = -6,
+    QK_GATE_T = -7,
+    QK_GATE_TDG = -8,
+    QK_GATE_U3 = -9,     /* params (theta, phi, lambda), OpenQASM U        */
+    QK_GATE_P = -10,     /* params (phi): diag(1, e^{i phi}); with one
+                            control this is CPHASE of Appendix A           */
+    QK_GATE_RZ = -11,    /* params (theta): diag(e^{-i theta/2}, e^{i theta/2}) */
+    QK_GATE_SWAP = -12   /* 2 targets (Appendix A SWAP after the QFT)      */
+};
+
+#define QK_MAX_QUBITS 36
+#define QK_MAX_CONTROLS 16
+#define QK_MAX_COND 16
+#define QK_MAX_MATRIX_QUBITS 6
+#define QK_MAX_PERM_QUBITS 30
+#define QK_MAX_RPHASE_CBITS 62
+
+/* Create a context with no qubits.  cuda_stream: a cudaStream_t to enqueue on
+ * (borrowed, must outlive the context), or NULL for a context-owned stream.
+ * opt may be NULL for defaults.  Errors: QK_EINVAL, QK_ECUDA. */
+qk_status qk_create(qk_ctx **out, qk_precision precision, void *cuda_stream, const qk_options *opt);
+
+/* Free every device and host resource of the context (waits for its stream). */
+qk_status qk_destroy(qk_ctx *ctx);
+
+/* "AddQubits" (Q-Kit section, Appendix A): append n qubits in |0> as the new
+ * highest index bits (the state becomes |0...0> (x) psi).  *first_qubit_out (may
+ * be NULL) receives the first new qubit's id.  Errors: QK_EINVAL (n < 1 or total
+ * above QK_MAX_QUBITS), QK_EBUDGET, QK_ENOMEM. */
+qk_status qk_add_qubits(qk_ctx *ctx, int n, int *first_qubit_out);
+
+/* "AddCbits" (Appendix A): append n classical bits, initialised to 0. */
+qk_status qk_add_cbits(qk_ctx *ctx, int n, int *first_cbit_out);
+
+/* Define a gate "as a matrix" (Q-Kit section, command 4): k qubits (1..6), u is the
+ * 2^k x 2^k matrix, row-major, interleaved (re, im) doubles, copied.  The matrix
+ * must satisfy max |U^dagger U - I| <= unitarity_tol (QK_ENOTUNITARY otherwise).
+ * *gate_id receives an id >= 0 valid for the life of the context. */
+qk_status qk_define_gate_matrix(qk_ctx *ctx, int k, const double *u, double unitarity_tol, int *gate_id);
+
+/* Define a gate "as a function" (Q-Kit section, command 4; QuModExpUaj of
+ * Appendix A): on a w-qubit register (1..30), x -> c*x mod N for x < N and x
+ * unchanged for x >= N.  Requires 2 <= N <= 2^w, c < N and gcd(c, N) = 1
+ * (QK_ENOTBIJECTIVE otherwise).  Index arithmetic is exact (64-bit). */
+qk_status qk_define_gate_perm_mulmod(qk_ctx *ctx, int w, uint64_t c, uint64_t N, int *gate_id);
+
+/* Define a gate as an arbitrary function f on a w-qubit register value (1..24):
+ * f is 2^w entries, copied, and must be a bijection (QK_ENOTBIJECTIVE). */
+qk_status qk_define_gate_perm_table(qk_ctx *ctx, int w, const uint64_t *f, int *gate_id);
+
+/* "GateOp" (Q-Kit section, command 2; Appendix A): apply a built-in or defined
+ * gate.  targets: nt qubits (1 for 1-qubit built-ins, 2 for SWAP, k or w for
+ * defined gates; first-listed = register MSB).  controls: nc quantum controls
+ * (the gate acts where all are |1>).  cond_cbits: ncc classical bits that must
+ * all be 1 for the gate to act (checked on the device when the gate runs; the
+ * classically controlled "SigmaX 0,-k" of Appendix A).  params: np doubles for
+ * parametrised built-ins.  Targets, controls must be distinct and in range. */
+qk_status qk_apply_gate(qk_ctx *ctx, int gate_id, const int *targets, int nt,
+                        const int *controls, int nc, const int *cond_cbits, int ncc,
+                        const double *params, int np);
+
+/* "RPhase 0,-e..-1" (Appendix A, nx2n branch): multiply the |1> component of
+ * target by exp(i theta), theta = -2 pi sum_{l=1..ncb} c[cbits[l-1]] / 2^(l+1),
+ * where cbits lists the classical bits most recent first.  The angle is formed on
+ * the device from the cbit values (no host round trip).  ncb <= 62. */
+qk_status qk_apply_rphase_cbits(qk_ctx *ctx, int target, const int *cbits, int ncb);
+
+/* "Measure" (Q-Kit section, command 3) with "Copy" into classical bits:
+ * measures qubits[0..nq-1] one after another in list order.  For each, P0 is the
+ * probability of reading 0 (summed in FP64 on the device), the outcome is
+ * m = (uniforms[i] >= P0), the other branch is zeroed and the kept branch scaled
+ * by 1/sqrt(P_m).  uniforms: nq values in [0, 1), copied.  dest_cbits: nq cbits
+ * to receive the outcomes, or NULL.  outcome: if non-NULL, the call waits and
+ * stores the register value (first-listed qubit = MSB); if NULL it returns
+ * without waiting. */
+qk_status qk_measure(qk_ctx *ctx, const int *qubits, int nq, const double *uniforms,
+                     const int *dest_cbits, uint64_t *outcome);
+
+/* Copy n classical bits starting at cbit 0 to host (waits for the stream). */
+qk_status qk_read_cbits(qk_ctx *ctx, uint8_t *out, int n);
+
+/* Overwrite cbits[first..first+n-1] with values 0/1 (stream-ordered). */
+qk_status qk_write_cbits(qk_ctx *ctx, int first, const uint8_t *in, int n);
+
+/* Copy the whole state (2^n amplitudes, logical qubit order) into a host buffer
+ * of exactly bytes = 2^n * sizeof(amplitude); waits for the stream. */
+qk_status qk_get_state(qk_ctx *ctx, void *host_out, size_t bytes);
+
+/* Overwrite the state from a host buffer of exactly 2^n amplitudes (logical
+ * order); the buffer is copied before the call returns. */
+qk_status qk_set_state(qk_ctx *ctx, const void *host_in, size_t bytes);
+
+/* Reset the state to |0...0> (stream-ordered, no host copy). */
+qk_status qk_reset(qk_ctx *ctx);
+
+/* Run every queued gate, undo qubit relabelling, and return the device pointer
+ * and size of the state (logical order).  The pointer stays valid until the next
+ * call on the context that changes the qubit count or applies a permutation
+ * gate.  Does not wait for the stream. */
+qk_status qk_device_state(qk_ctx *ctx, void **dptr, size_t *bytes);
+
+/* Run every queued gate (fused mode); stream-ordered, does not wait. */
+qk_status qk_flush(qk_ctx *ctx);
+
+/* Flush and wait until all work on the context's stream has finished. */
+qk_status qk_sync(qk_ctx *ctx);
+
+/* Number of qubits / cbits of the context. */
+int qk_num_qubits(const qk_ctx *ctx);
+int qk_num_cbits(const qk_ctx *ctx);
+
+/* Counters since creation or the last reset_counters: kernel launches, passes
+ * over the state (launches that stream the full state), and algorithmic bytes
+ * (2^n * amplitude size * 2 per full pass, read + write). */
+qk_status qk_get_counters(const qk_ctx *ctx, uint64_t *launches, uint64_t *state_passes,
+                          uint64_t *algorithmic_bytes);
+qk_status qk_reset_counters(qk_ctx *ctx);
+
+/* With options.profile = 1: per launch class (0 = tile pass, 1 = 2x2 pass, 2 =
+ * diagonal pass, 3 = k-qubit block, 4 = permutation, 5 = measurement, 6 = other)
+ * the launches, summed CUDA-event milliseconds and algorithmic bytes since the
+ * last reset.  Waits for the stream.  Errors: QK_ESTATE if profiling is off. */
+#define QK_NUM_LAUNCH_CLASSES 7
+qk_status qk_profile(qk_ctx *ctx, uint64_t launches[QK_NUM_LAUNCH_CLASSES],
+                     double ms[QK_NUM_LAUNCH_CLASSES], double bytes[QK_NUM_LAUNCH_CLASSES]);
+
+/* Message for the last failed call on this context ("" if none). */
+const char *qk_last_error(const qk_ctx *ctx);
+
+/* Human-readable name of a status code. */
+const char *qk_status_str(qk_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QK_H */

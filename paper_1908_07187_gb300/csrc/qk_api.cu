@@ -1,0 +1,931 @@
+// Host side of libqk: the C ABI of include/qk.h, gate decomposition into
+// device launches, qubit relabelling (SWAP), measurement sequencing and the
+// fused-mode queue.  All arithmetic on amplitudes happens in the kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "qk.h"
+#include "qk_kernels.cuh"
+#include "qk_plan.h"
+
+using cd = std::complex<double>;
+
+namespace {
+
+struct GateDef {
+    int kind = 0;                 // 0 = matrix, 1 = mul-mod, 2 = table
+    int k = 0;                    // matrix qubits, or register width w
+    std::vector<cd> m;            // FP64 master matrix (row-major)
+    bool diagonal = false;
+    void *d_mat = nullptr;        // working-precision copy on the device
+    uint64_t c = 0, N = 0, cinv = 0;
+    uint32_t *d_finv = nullptr;
+};
+
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+    double bytes;
+};
+
+constexpr int kMeasBlocksPerSM = 4;
+
+}  // namespace
+
+struct qk_ctx {
+    qk_precision prec = QK_C64;
+    size_t amp = 8;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int sms = 148;
+    qk_options opt{};
+
+    int n = 0;
+    void *d_state = nullptr;
+    void *d_scratch = nullptr;
+    size_t state_bytes = 0, scratch_bytes = 0;
+
+    int ncb = 0, cb_cap = 0;
+    uint8_t *d_cbits = nullptr;
+
+    double *d_partials = nullptr;
+    int meas_blocks = 0;
+    qk::MeasSlot *d_slots = nullptr;
+    int slot_cap = 0;
+
+    std::vector<int> l2p;          // logical -> physical qubit
+    std::vector<GateDef> gates;
+    void *d_swap_mat = nullptr;    // SWAP as a 4x4 matrix, for controlled SWAPs
+
+    std::vector<qk::FusedOp> pending;   // fused-mode queue (physical qubits)
+    qk::TilePlanner *planner = nullptr;
+
+    uint64_t launches = 0, passes_x1000 = 0;
+    double alg_bytes = 0.0;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    uint64_t prof_launches[QK_NUM_LAUNCH_CLASSES] = {};
+    double prof_ms[QK_NUM_LAUNCH_CLASSES] = {};
+    double prof_bytes[QK_NUM_LAUNCH_CLASSES] = {};
+
+    std::string err;
+};
+
+namespace {
+
+qk_status fail(qk_ctx *c, qk_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define CUDA_TRY(ctx, call)                                                                      \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail((ctx), QK_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));        \
+    } while (0)
+
+size_t full_pass_bytes(const qk_ctx *c) { return (size_t)2 * c->amp << c->n; }
+
+cudaEvent_t get_event(qk_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket a launch with CUDA events when profiling; count it either way.
+struct LaunchScope {
+    qk_ctx *c;
+    int cls;
+    double bytes;
+    cudaEvent_t a = nullptr;
+    LaunchScope(qk_ctx *c_, int cls_, double bytes_) : c(c_), cls(cls_), bytes(bytes_) {
+        if (c->opt.profile) {
+            a = get_event(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~LaunchScope() {
+        c->launches++;
+        c->alg_bytes += bytes;
+        const double fp = (double)full_pass_bytes(c);
+        if (fp > 0) c->passes_x1000 += (uint64_t)llround(1000.0 * bytes / fp);
+        if (c->opt.profile) {
+            cudaEvent_t b = get_event(c);
+            cudaEventRecord(b, c->stream);
+            c->prof.push_back({cls, a, b, bytes});
+        }
+    }
+};
+
+bool valid_qubits(const qk_ctx *c, const int *q, int k) {
+    if (k < 0 || (k > 0 && !q)) return false;
+    for (int a = 0; a < k; ++a) {
+        if (q[a] < 0 || q[a] >= c->n) return false;
+        for (int b = 0; b < a; ++b)
+            if (q[a] == q[b]) return false;
+    }
+    return true;
+}
+
+bool fill_cond(qk_ctx *c, qk::Cond &cond, const int *cb, int ncc) {
+    if (ncc < 0 || ncc > qk::kMaxCond || (ncc > 0 && !cb)) return false;
+    cond.n = ncc;
+    for (int a = 0; a < ncc; ++a) {
+        if (cb[a] < 0 || cb[a] >= c->ncb) return false;
+        cond.idx[a] = cb[a];
+    }
+    return true;
+}
+
+void set_positions(qk::Positions &p, std::vector<int> v) {
+    std::sort(v.begin(), v.end());
+    p.n = (int)v.size();
+    for (int a = 0; a < p.n; ++a) p.pos[a] = v[a];
+}
+
+// Upload a matrix in the working precision.
+qk_status upload_matrix(qk_ctx *c, const std::vector<cd> &m, void **dptr) {
+    const size_t cnt = m.size();
+    std::vector<unsigned char> host(cnt * c->amp);
+    for (size_t i = 0; i < cnt; ++i) {
+        if (c->prec == QK_C64) {
+            float v[2] = {(float)m[i].real(), (float)m[i].imag()};
+            memcpy(&host[i * 8], v, 8);
+        } else {
+            double v[2] = {m[i].real(), m[i].imag()};
+            memcpy(&host[i * 16], v, 16);
+        }
+    }
+    CUDA_TRY(c, cudaMalloc(dptr, host.size()));
+    CUDA_TRY(c, cudaMemcpy(*dptr, host.data(), host.size(), cudaMemcpyHostToDevice));
+    return QK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// built-in gate matrices (textbook definitions; FP64)
+// ---------------------------------------------------------------------------
+bool builtin_matrix(int id, const double *p, int np, cd m[4], int &ntargets) {
+    const double r2 = 1.0 / std::sqrt(2.0);
+    const cd I(0, 1);
+    ntargets = 1;
+    switch (id) {
+        case QK_GATE_X: m[0] = 0; m[1] = 1; m[2] = 1; m[3] = 0; return np == 0;
+        case QK_GATE_Y: m[0] = 0; m[1] = -I; m[2] = I; m[3] = 0; return np == 0;
+        case QK_GATE_Z: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = -1; return np == 0;
+        case QK_GATE_H: m[0] = r2; m[1] = r2; m[2] = r2; m[3] = -r2; return np == 0;
+        case QK_GATE_S: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = I; return np == 0;
+        case QK_GATE_SDG: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = -I; return np == 0;
+        case QK_GATE_T: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = std::polar(1.0, M_PI / 4); return np == 0;
+        case QK_GATE_TDG: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = std::polar(1.0, -M_PI / 4); return np == 0;
+        case QK_GATE_U3: {
+            if (np != 3 || !p) return false;
+            const double c = std::cos(p[0] / 2), s = std::sin(p[0] / 2);
+            m[0] = c;
+            m[1] = -std::polar(1.0, p[2]) * s;
+            m[2] = std::polar(1.0, p[1]) * s;
+            m[3] = std::polar(1.0, p[1] + p[2]) * c;
+            return true;
+        }
+        case QK_GATE_P:
+            if (np != 1 || !p) return false;
+            m[0] = 1; m[1] = 0; m[2] = 0; m[3] = std::polar(1.0, p[0]);
+            return true;
+        case QK_GATE_RZ:
+            if (np != 1 || !p) return false;
+            m[0] = std::polar(1.0, -p[0] / 2); m[1] = 0; m[2] = 0; m[3] = std::polar(1.0, p[0] / 2);
+            return true;
+        case QK_GATE_SWAP: ntargets = 2; return np == 0;
+        default: return false;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// plain execution of one fused-queue op
+// ---------------------------------------------------------------------------
+qk_status run_op_plain(qk_ctx *c, const qk::FusedOp &op) {
+    const int n = c->n;
+    if (op.kind == qk::FusedOp::U2) {
+        qk::U2Args a{};
+        for (int i = 0; i < 4; ++i) {
+            a.m[2 * i] = op.m[i].real();
+            a.m[2 * i + 1] = op.m[i].imag();
+        }
+        a.cmask = op.cmask;
+        a.q = op.q;
+        std::vector<int> pos{op.q};
+        for (int b = 0; b < n; ++b)
+            if ((op.cmask >> b) & 1) pos.push_back(b);
+        set_positions(a.ins, pos);
+        a.n_units = 1ull << (n - (int)pos.size());
+        a.cond = op.cond;
+        LaunchScope ls(c, 1, (double)2 * c->amp * (double)(1ull << (n - (int)pos.size() + 1)));
+        CUDA_TRY(c, qk::launch_u2((int)c->prec, c->d_state, a, c->d_cbits, n, c->sms, c->stream));
+    } else if (op.kind == qk::FusedOp::PHASE) {
+        qk::PhaseArgs a{};
+        a.f_re = op.f.real();
+        a.f_im = op.f.imag();
+        a.mask = op.mask;
+        a.val = op.val;
+        std::vector<int> pos;
+        for (int b = 0; b < n; ++b)
+            if ((op.mask >> b) & 1) pos.push_back(b);
+        set_positions(a.ins, pos);
+        a.n_units = 1ull << (n - (int)pos.size());
+        a.cond = op.cond;
+        a.n_rphase = 0;
+        LaunchScope ls(c, 2, (double)2 * c->amp * (double)a.n_units);
+        CUDA_TRY(c, qk::launch_phase((int)c->prec, c->d_state, a, c->d_cbits, c->sms, c->stream));
+    } else {
+        return fail(c, QK_EINVAL, "internal: unknown queued op kind");
+    }
+    return QK_OK;
+}
+
+qk_status flush(qk_ctx *c) {
+    if (c->pending.empty()) return QK_OK;
+    qk_status st = QK_OK;
+    if (c->opt.exec_mode == QK_EXEC_FUSED && c->planner) {
+        st = qk::run_fused(c->planner, c, c->pending);
+    } else {
+        for (const auto &op : c->pending) {
+            st = run_op_plain(c, op);
+            if (st != QK_OK) break;
+        }
+    }
+    c->pending.clear();
+    return st;
+}
+
+qk_status enqueue(qk_ctx *c, const qk::FusedOp &op) {
+    if (c->opt.exec_mode == QK_EXEC_PLAIN) return run_op_plain(c, op);
+    c->pending.push_back(op);
+    if ((int)c->pending.size() >= c->opt.max_pending) return flush(c);
+    return QK_OK;
+}
+
+// Queue a (controlled) 1-qubit matrix on physical qubit q.
+qk_status apply_1q(qk_ctx *c, const cd m[4], int q, uint64_t cmask, const qk::Cond &cond) {
+    const uint64_t tb = 1ull << q;
+    if (m[1] == 0.0 && m[2] == 0.0) {
+        // diagonal: one phase op per entry that differs from 1
+        if (m[0] != 1.0) {
+            qk::FusedOp op;
+            op.kind = qk::FusedOp::PHASE;
+            op.mask = cmask | tb;
+            op.val = cmask;
+            op.f = m[0];
+            op.cond = cond;
+            qk_status s = enqueue(c, op);
+            if (s != QK_OK) return s;
+        }
+        if (m[3] != 1.0) {
+            qk::FusedOp op;
+            op.kind = qk::FusedOp::PHASE;
+            op.mask = cmask | tb;
+            op.val = cmask | tb;
+            op.f = m[3];
+            op.cond = cond;
+            return enqueue(c, op);
+        }
+        return QK_OK;
+    }
+    qk::FusedOp op;
+    op.kind = qk::FusedOp::U2;
+    op.q = q;
+    op.cmask = cmask;
+    for (int i = 0; i < 4; ++i) op.m[i] = m[i];
+    op.cond = cond;
+    return enqueue(c, op);
+}
+
+qk_status ensure_scratch(qk_ctx *c) {
+    if (c->d_scratch && c->scratch_bytes == c->state_bytes) return QK_OK;
+    if (c->d_scratch) cudaFree(c->d_scratch);
+    c->d_scratch = nullptr;
+    c->scratch_bytes = 0;
+    if (c->opt.hbm_budget_bytes && 2 * c->state_bytes > c->opt.hbm_budget_bytes)
+        return fail(c, QK_EBUDGET, "permutation scratch (%zu bytes) exceeds the HBM budget", c->state_bytes);
+    if (cudaMalloc(&c->d_scratch, c->state_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, QK_ENOMEM, "cannot allocate %zu bytes of permutation scratch", c->state_bytes);
+    }
+    c->scratch_bytes = c->state_bytes;
+    return QK_OK;
+}
+
+// Physically reorder the state so that logical qubit q is physical bit q.
+qk_status canonicalize(qk_ctx *c) {
+    bool ident = true;
+    for (int q = 0; q < c->n; ++q) ident = ident && c->l2p[q] == q;
+    if (ident) return QK_OK;
+    qk_status s = ensure_scratch(c);
+    if (s != QK_OK) return s;
+    qk::RelabelArgs a{};
+    a.n = c->n;
+    for (int q = 0; q < c->n; ++q) a.phys_of[q] = c->l2p[q];
+    a.n_amps = 1ull << c->n;
+    {
+        LaunchScope ls(c, 6, (double)full_pass_bytes(c));
+        CUDA_TRY(c, qk::launch_relabel((int)c->prec, c->d_state, c->d_scratch, a, c->sms, c->stream));
+    }
+    std::swap(c->d_state, c->d_scratch);
+    for (int q = 0; q < c->n; ++q) c->l2p[q] = q;
+    return QK_OK;
+}
+
+qk_status ensure_slots(qk_ctx *c, int nq) {
+    if (nq <= c->slot_cap) return QK_OK;
+    if (c->d_slots) cudaFree(c->d_slots);
+    c->d_slots = nullptr;
+    int cap = std::max(nq, 64);
+    CUDA_TRY(c, cudaMalloc(&c->d_slots, sizeof(qk::MeasSlot) * cap));
+    c->slot_cap = cap;
+    return QK_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// fused-mode hooks used by the planner (qk_plan.cu)
+// ===========================================================================
+namespace qk {
+void *ctx_state(qk_ctx *c) { return c->d_state; }
+int ctx_n(qk_ctx *c) { return c->n; }
+int ctx_prec(qk_ctx *c) { return (int)c->prec; }
+int ctx_sms(qk_ctx *c) { return c->sms; }
+int ctx_tile_qubits(qk_ctx *c) { return c->opt.tile_qubits; }
+cudaStream_t ctx_stream(qk_ctx *c) { return c->stream; }
+const uint8_t *ctx_cbits(qk_ctx *c) { return c->d_cbits; }
+qk_status ctx_run_plain(qk_ctx *c, const FusedOp &op) { return run_op_plain(c, op); }
+qk_status ctx_fail(qk_ctx *c, qk_status s, const char *msg) { return fail(c, s, "%s", msg); }
+void ctx_launch_begin(qk_ctx *c, int cls, double bytes, void **token) {
+    *token = new LaunchScope(c, cls, bytes);
+}
+void ctx_launch_end(void *token) { delete static_cast<LaunchScope *>(token); }
+}  // namespace qk
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *qk_status_str(qk_status s) {
+    switch (s) {
+        case QK_OK: return "QK_OK";
+        case QK_EINVAL: return "QK_EINVAL";
+        case QK_ENOMEM: return "QK_ENOMEM";
+        case QK_EBUDGET: return "QK_EBUDGET";
+        case QK_ENOTBIJECTIVE: return "QK_ENOTBIJECTIVE";
+        case QK_ENOTUNITARY: return "QK_ENOTUNITARY";
+        case QK_ECUDA: return "QK_ECUDA";
+        case QK_ETIMEOUT: return "QK_ETIMEOUT";
+        case QK_ESTATE: return "QK_ESTATE";
+    }
+    return "unknown";
+}
+
+qk_status qk_create(qk_ctx **out, qk_precision precision, void *cuda_stream, const qk_options *opt) {
+    if (!out) return QK_EINVAL;
+    *out = nullptr;
+    if (precision != QK_C64 && precision != QK_C128) return QK_EINVAL;
+    qk_ctx *c = new (std::nothrow) qk_ctx();
+    if (!c) return QK_ENOMEM;
+    c->prec = precision;
+    c->amp = precision == QK_C64 ? 8 : 16;
+    if (opt) {
+        c->opt = *opt;
+        for (int r : opt->reserved)
+            if (r != 0) { delete c; return QK_EINVAL; }
+    } else {
+        c->opt.exec_mode = QK_EXEC_FUSED;
+    }
+    if (c->opt.exec_mode != QK_EXEC_PLAIN && c->opt.exec_mode != QK_EXEC_FUSED) { delete c; return QK_EINVAL; }
+    if (c->opt.max_pending <= 0) c->opt.max_pending = 4096;
+    if (c->opt.tile_qubits < 0 || c->opt.tile_qubits > 16) { delete c; return QK_EINVAL; }
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return QK_ECUDA;
+    }
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return QK_ECUDA; }
+        c->own_stream = true;
+    }
+    c->meas_blocks = c->sms * kMeasBlocksPerSM;
+    if (cudaMalloc(&c->d_partials, sizeof(double) * 2 * c->meas_blocks) != cudaSuccess) {
+        qk_destroy(c);
+        return QK_ENOMEM;
+    }
+    std::vector<cd> sw = {1, 0, 0, 0, 0, 0, 1, 0, 0, 1, 0, 0, 0, 0, 0, 1};
+    if (upload_matrix(c, sw, &c->d_swap_mat) != QK_OK) { qk_destroy(c); return QK_ECUDA; }
+    c->planner = qk::make_planner();
+    *out = c;
+    return QK_OK;
+}
+
+qk_status qk_destroy(qk_ctx *c) {
+    if (!c) return QK_EINVAL;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &p : c->prof) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto &g : c->gates) {
+        if (g.d_mat) cudaFree(g.d_mat);
+        if (g.d_finv) cudaFree(g.d_finv);
+    }
+    if (c->d_swap_mat) cudaFree(c->d_swap_mat);
+    if (c->d_state) cudaFree(c->d_state);
+    if (c->d_scratch) cudaFree(c->d_scratch);
+    if (c->d_cbits) cudaFree(c->d_cbits);
+    if (c->d_partials) cudaFree(c->d_partials);
+    if (c->d_slots) cudaFree(c->d_slots);
+    if (c->planner) qk::free_planner(c->planner);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return QK_OK;
+}
+
+qk_status qk_add_qubits(qk_ctx *c, int k, int *first) {
+    if (!c) return QK_EINVAL;
+    if (k < 1 || c->n + k > QK_MAX_QUBITS) return fail(c, QK_EINVAL, "add_qubits: bad count %d (have %d)", k, c->n);
+    qk_status s = flush(c);
+    if (s != QK_OK) return s;
+    s = canonicalize(c);
+    if (s != QK_OK) return s;
+    const int nn = c->n + k;
+    const size_t bytes = c->amp << nn;
+    if (c->opt.hbm_budget_bytes && bytes > c->opt.hbm_budget_bytes)
+        return fail(c, QK_EBUDGET, "state of %d qubits (%zu bytes) exceeds the HBM budget", nn, bytes);
+    void *d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, QK_ENOMEM, "cannot allocate %zu bytes for %d qubits", bytes, nn);
+    }
+    CUDA_TRY(c, cudaMemsetAsync(d, 0, bytes, c->stream));
+    if (c->d_state) {
+        CUDA_TRY(c, cudaMemcpyAsync(d, c->d_state, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->d_state);
+    } else {
+        CUDA_TRY(c, qk::launch_set_basis((int)c->prec, d, 0, c->stream));
+    }
+    if (c->d_scratch) {
+        cudaFree(c->d_scratch);
+        c->d_scratch = nullptr;
+        c->scratch_bytes = 0;
+    }
+    if (first) *first = c->n;
+    for (int q = c->n; q < nn; ++q) c->l2p.push_back(q);
+    c->d_state = d;
+    c->state_bytes = bytes;
+    c->n = nn;
+    return QK_OK;
+}
+
+qk_status qk_add_cbits(qk_ctx *c, int k, int *first) {
+    if (!c) return QK_EINVAL;
+    if (k < 1 || c->ncb + k > (1 << 20)) return fail(c, QK_EINVAL, "add_cbits: bad count %d", k);
+    if (c->ncb + k > c->cb_cap) {
+        int cap = std::max(c->ncb + k, std::max(64, 2 * c->cb_cap));
+        uint8_t *d = nullptr;
+        CUDA_TRY(c, cudaMalloc(&d, cap));
+        CUDA_TRY(c, cudaMemsetAsync(d, 0, cap, c->stream));
+        if (c->d_cbits) {
+            CUDA_TRY(c, cudaMemcpyAsync(d, c->d_cbits, c->ncb, cudaMemcpyDeviceToDevice, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            cudaFree(c->d_cbits);
+        }
+        c->d_cbits = d;
+        c->cb_cap = cap;
+    }
+    if (first) *first = c->ncb;
+    c->ncb += k;
+    return QK_OK;
+}
+
+qk_status qk_define_gate_matrix(qk_ctx *c, int k, const double *u, double tol, int *gate_id) {
+    if (!c) return QK_EINVAL;
+    if (k < 1 || k > QK_MAX_MATRIX_QUBITS || !u || !gate_id || !(tol >= 0))
+        return fail(c, QK_EINVAL, "define_gate_matrix: bad arguments");
+    const int d = 1 << k;
+    GateDef g;
+    g.kind = 0;
+    g.k = k;
+    g.m.resize((size_t)d * d);
+    for (int i = 0; i < d * d; ++i) g.m[i] = cd(u[2 * i], u[2 * i + 1]);
+    double dev = 0.0;
+    for (int r = 0; r < d; ++r)
+        for (int cc = 0; cc < d; ++cc) {
+            cd s = 0;
+            for (int x = 0; x < d; ++x) s += std::conj(g.m[x * d + r]) * g.m[x * d + cc];
+            dev = std::max(dev, std::abs(s - (r == cc ? 1.0 : 0.0)));
+        }
+    if (!(dev <= tol)) return fail(c, QK_ENOTUNITARY, "matrix is not unitary: max |U^H U - I| = %g", dev);
+    g.diagonal = true;
+    for (int r = 0; r < d; ++r)
+        for (int cc = 0; cc < d; ++cc)
+            if (r != cc && g.m[r * d + cc] != 0.0) g.diagonal = false;
+    qk_status s = upload_matrix(c, g.m, &g.d_mat);
+    if (s != QK_OK) return s;
+    *gate_id = (int)c->gates.size();
+    c->gates.push_back(std::move(g));
+    return QK_OK;
+}
+
+static uint64_t modinv(uint64_t a, uint64_t N, bool &ok) {
+    // extended Euclid on signed 128-bit
+    __int128 t = 0, nt = 1, r = (__int128)N, nr = (__int128)(a % N);
+    while (nr != 0) {
+        __int128 q = r / nr, tmp;
+        tmp = t - q * nt; t = nt; nt = tmp;
+        tmp = r - q * nr; r = nr; nr = tmp;
+    }
+    ok = (r == 1);
+    if (t < 0) t += N;
+    return (uint64_t)t;
+}
+
+qk_status qk_define_gate_perm_mulmod(qk_ctx *c, int w, uint64_t cc, uint64_t N, int *gate_id) {
+    if (!c) return QK_EINVAL;
+    if (w < 1 || w > QK_MAX_PERM_QUBITS || !gate_id || N < 2 || N > (1ull << w))
+        return fail(c, QK_EINVAL, "define_gate_perm_mulmod: bad w=%d or N=%llu", w, (unsigned long long)N);
+    if (cc >= N) return fail(c, QK_EINVAL, "define_gate_perm_mulmod: c must be < N");
+    bool ok = false;
+    uint64_t inv = modinv(cc, N, ok);
+    if (!ok) return fail(c, QK_ENOTBIJECTIVE, "x -> %llu x mod %llu is not a permutation (gcd != 1)",
+                         (unsigned long long)cc, (unsigned long long)N);
+    GateDef g;
+    g.kind = 1;
+    g.k = w;
+    g.c = cc;
+    g.N = N;
+    g.cinv = inv;
+    *gate_id = (int)c->gates.size();
+    c->gates.push_back(std::move(g));
+    return QK_OK;
+}
+
+qk_status qk_define_gate_perm_table(qk_ctx *c, int w, const uint64_t *f, int *gate_id) {
+    if (!c) return QK_EINVAL;
+    if (w < 1 || w > 24 || !f || !gate_id) return fail(c, QK_EINVAL, "define_gate_perm_table: bad arguments");
+    const uint64_t d = 1ull << w;
+    std::vector<uint32_t> inv(d, 0xffffffffu);
+    for (uint64_t x = 0; x < d; ++x) {
+        if (f[x] >= d || inv[f[x]] != 0xffffffffu)
+            return fail(c, QK_ENOTBIJECTIVE, "table is not a permutation (entry %llu)", (unsigned long long)x);
+        inv[f[x]] = (uint32_t)x;
+    }
+    GateDef g;
+    g.kind = 2;
+    g.k = w;
+    CUDA_TRY(c, cudaMalloc(&g.d_finv, sizeof(uint32_t) * d));
+    CUDA_TRY(c, cudaMemcpy(g.d_finv, inv.data(), sizeof(uint32_t) * d, cudaMemcpyHostToDevice));
+    *gate_id = (int)c->gates.size();
+    c->gates.push_back(std::move(g));
+    return QK_OK;
+}
+
+qk_status qk_apply_gate(qk_ctx *c, int gate_id, const int *targets, int nt, const int *controls, int nc,
+                        const int *cond_cbits, int ncc, const double *params, int np) {
+    if (!c) return QK_EINVAL;
+    if (c->n == 0) return fail(c, QK_ESTATE, "apply_gate: no qubits");
+    if (nc < 0 || nc > QK_MAX_CONTROLS || !valid_qubits(c, targets, nt) || !valid_qubits(c, controls, nc))
+        return fail(c, QK_EINVAL, "apply_gate: bad target or control list");
+    for (int a = 0; a < nt; ++a)
+        for (int b = 0; b < nc; ++b)
+            if (targets[a] == controls[b]) return fail(c, QK_EINVAL, "apply_gate: qubit %d is target and control", targets[a]);
+    qk::Cond cond{};
+    if (!fill_cond(c, cond, cond_cbits, ncc)) return fail(c, QK_EINVAL, "apply_gate: bad classical condition");
+    if (np < 0 || (np > 0 && !params)) return fail(c, QK_EINVAL, "apply_gate: bad params");
+
+    uint64_t cmask = 0;
+    for (int b = 0; b < nc; ++b) cmask |= 1ull << c->l2p[controls[b]];
+
+    if (gate_id < 0) {
+        cd m[4];
+        int ntg = 0;
+        if (!builtin_matrix(gate_id, params, np, m, ntg)) return fail(c, QK_EINVAL, "apply_gate: unknown built-in %d or bad params", gate_id);
+        if (nt != ntg) return fail(c, QK_EINVAL, "apply_gate: built-in %d takes %d targets", gate_id, ntg);
+        if (gate_id == QK_GATE_SWAP) {
+            if (nc == 0 && ncc == 0) {
+                // SWAP without controls: relabel logical -> physical, no data movement
+                qk_status s = QK_OK;
+                std::swap(c->l2p[targets[0]], c->l2p[targets[1]]);
+                return s;
+            }
+            // controlled or classically conditioned SWAP: dense 4x4 block
+            qk_status s = flush(c);
+            if (s != QK_OK) return s;
+            qk::MatKArgs a{};
+            a.k = 2;
+            a.tpos[0] = c->l2p[targets[0]];
+            a.tpos[1] = c->l2p[targets[1]];
+            a.cmask = cmask;
+            std::vector<int> pos{a.tpos[0], a.tpos[1]};
+            for (int b = 0; b < nc; ++b) pos.push_back(c->l2p[controls[b]]);
+            set_positions(a.ins, pos);
+            a.n_groups = 1ull << (c->n - (int)pos.size());
+            a.mat = c->d_swap_mat;
+            a.cond = cond;
+            LaunchScope ls(c, 3, (double)2 * c->amp * (double)(a.n_groups << 2));
+            CUDA_TRY(c, qk::launch_matk((int)c->prec, c->d_state, a, c->d_cbits, c->sms, c->stream));
+            return QK_OK;
+        }
+        return apply_1q(c, m, c->l2p[targets[0]], cmask, cond);
+    }
+
+    if (gate_id >= (int)c->gates.size()) return fail(c, QK_EINVAL, "apply_gate: unknown gate id %d", gate_id);
+    const GateDef &g = c->gates[gate_id];
+    if (nt != g.k) return fail(c, QK_EINVAL, "apply_gate: gate %d takes %d targets, got %d", gate_id, g.k, nt);
+    if (g.kind == 0) {
+        if (g.k == 1) {
+            cd m[4] = {g.m[0], g.m[1], g.m[2], g.m[3]};
+            return apply_1q(c, m, c->l2p[targets[0]], cmask, cond);
+        }
+        const int d = 1 << g.k;
+        if (g.diagonal) {
+            int nonunit = 0;
+            for (int x = 0; x < d; ++x) nonunit += (g.m[x * d + x] != 1.0);
+            if (nonunit <= 2) {
+                for (int x = 0; x < d; ++x) {
+                    if (g.m[x * d + x] == 1.0) continue;
+                    qk::FusedOp op;
+                    op.kind = qk::FusedOp::PHASE;
+                    op.mask = cmask;
+                    op.val = cmask;
+                    for (int a = 0; a < g.k; ++a) {
+                        const uint64_t tb = 1ull << c->l2p[targets[a]];
+                        op.mask |= tb;
+                        if ((x >> (g.k - 1 - a)) & 1) op.val |= tb;
+                    }
+                    op.f = g.m[x * d + x];
+                    op.cond = cond;
+                    qk_status s = enqueue(c, op);
+                    if (s != QK_OK) return s;
+                }
+                return QK_OK;
+            }
+        }
+        qk_status s = flush(c);
+        if (s != QK_OK) return s;
+        qk::MatKArgs a{};
+        a.k = g.k;
+        std::vector<int> pos;
+        for (int t = 0; t < g.k; ++t) {
+            a.tpos[t] = c->l2p[targets[t]];
+            pos.push_back(a.tpos[t]);
+        }
+        for (int b = 0; b < nc; ++b) pos.push_back(c->l2p[controls[b]]);
+        set_positions(a.ins, pos);
+        a.cmask = cmask;
+        a.n_groups = 1ull << (c->n - (int)pos.size());
+        a.mat = g.d_mat;
+        a.cond = cond;
+        LaunchScope ls(c, 3, (double)2 * c->amp * (double)(a.n_groups << g.k));
+        CUDA_TRY(c, qk::launch_matk((int)c->prec, c->d_state, a, c->d_cbits, c->sms, c->stream));
+        return QK_OK;
+    }
+    // permutation gates: out-of-place gather into scratch, then swap buffers
+    qk_status s = flush(c);
+    if (s != QK_OK) return s;
+    s = ensure_scratch(c);
+    if (s != QK_OK) return s;
+    qk::PermArgs a{};
+    a.w = g.k;
+    for (int t = 0; t < g.k; ++t) a.rpos[t] = c->l2p[targets[t]];
+    a.cmask = cmask;
+    a.n_amps = 1ull << c->n;
+    a.kind = g.kind == 1 ? 0 : 1;
+    a.N = g.N;
+    a.cinv = g.cinv;
+    a.mu = g.kind == 1 ? (~0ull) / g.N : 0;
+    a.finv = g.d_finv;
+    a.cond = cond;
+    {
+        LaunchScope ls(c, 4, (double)2 * c->amp * (double)(1ull << (c->n - nc)));
+        CUDA_TRY(c, qk::launch_perm((int)c->prec, c->d_state, c->d_scratch, a, c->d_cbits, c->sms, c->stream));
+    }
+    std::swap(c->d_state, c->d_scratch);
+    return QK_OK;
+}
+
+qk_status qk_apply_rphase_cbits(qk_ctx *c, int target, const int *cbits, int ncb) {
+    if (!c) return QK_EINVAL;
+    if (c->n == 0) return fail(c, QK_ESTATE, "apply_rphase_cbits: no qubits");
+    if (target < 0 || target >= c->n) return fail(c, QK_EINVAL, "apply_rphase_cbits: bad target");
+    if (ncb < 0 || ncb > QK_MAX_RPHASE_CBITS || (ncb > 0 && !cbits))
+        return fail(c, QK_EINVAL, "apply_rphase_cbits: bad cbit list");
+    for (int a = 0; a < ncb; ++a)
+        if (cbits[a] < 0 || cbits[a] >= c->ncb) return fail(c, QK_EINVAL, "apply_rphase_cbits: cbit %d out of range", cbits[a]);
+    if (ncb == 0) return QK_OK;
+    qk_status s = flush(c);
+    if (s != QK_OK) return s;
+    qk::PhaseArgs a{};
+    const int q = c->l2p[target];
+    a.mask = 1ull << q;
+    a.val = 1ull << q;
+    set_positions(a.ins, {q});
+    a.n_units = 1ull << (c->n - 1);
+    a.n_rphase = ncb;
+    for (int l = 0; l < ncb; ++l) a.rphase_idx[l] = cbits[l];
+    a.f_re = 1.0;
+    a.f_im = 0.0;
+    LaunchScope ls(c, 2, (double)2 * c->amp * (double)a.n_units);
+    CUDA_TRY(c, qk::launch_phase((int)c->prec, c->d_state, a, c->d_cbits, c->sms, c->stream));
+    return QK_OK;
+}
+
+qk_status qk_measure(qk_ctx *c, const int *qubits, int nq, const double *uniforms, const int *dest, uint64_t *outcome) {
+    if (!c) return QK_EINVAL;
+    if (c->n == 0) return fail(c, QK_ESTATE, "measure: no qubits");
+    if (nq < 1 || nq > 64 || !valid_qubits(c, qubits, nq) || !uniforms)
+        return fail(c, QK_EINVAL, "measure: bad qubit list (1..64 distinct qubits)");
+    for (int a = 0; a < nq; ++a) {
+        if (!(uniforms[a] >= 0.0 && uniforms[a] < 1.0)) return fail(c, QK_EINVAL, "measure: uniform %d not in [0, 1)", a);
+        if (dest && (dest[a] < 0 || dest[a] >= c->ncb)) return fail(c, QK_EINVAL, "measure: destination cbit %d out of range", dest[a]);
+    }
+    qk_status s = flush(c);
+    if (s != QK_OK) return s;
+    s = ensure_slots(c, nq);
+    if (s != QK_OK) return s;
+    const double fp = (double)full_pass_bytes(c);
+    for (int a = 0; a < nq; ++a) {
+        const int q = c->l2p[qubits[a]];
+        {
+            LaunchScope ls(c, 5, fp / 2);
+            CUDA_TRY(c, qk::launch_measure_reduce((int)c->prec, c->d_state, c->n, q, c->d_partials, c->meas_blocks, c->stream));
+        }
+        {
+            LaunchScope ls(c, 6, 0);
+            CUDA_TRY(c, qk::launch_measure_decide(c->d_partials, c->meas_blocks, uniforms[a], c->d_slots + a, c->d_cbits,
+                                                  dest ? dest[a] : -1, c->stream));
+        }
+        {
+            LaunchScope ls(c, 5, fp);
+            CUDA_TRY(c, qk::launch_measure_collapse((int)c->prec, c->d_state, c->n, q, c->d_slots + a, c->sms, c->stream));
+        }
+    }
+    if (outcome) {
+        std::vector<qk::MeasSlot> h(nq);
+        CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->d_slots, sizeof(qk::MeasSlot) * nq, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        uint64_t v = 0;
+        for (int a = 0; a < nq; ++a) v = (v << 1) | (uint64_t)(h[a].m & 1);
+        *outcome = v;
+    }
+    return QK_OK;
+}
+
+qk_status qk_read_cbits(qk_ctx *c, uint8_t *out, int n) {
+    if (!c) return QK_EINVAL;
+    if (n < 0 || n > c->ncb || (n > 0 && !out)) return fail(c, QK_EINVAL, "read_cbits: bad count");
+    qk_status s = flush(c);
+    if (s != QK_OK) return s;
+    if (n > 0) CUDA_TRY(c, cudaMemcpyAsync(out, c->d_cbits, n, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return QK_OK;
+}
+
+qk_status qk_write_cbits(qk_ctx *c, int first, const uint8_t *in, int n) {
+    if (!c) return QK_EINVAL;
+    if (first < 0 || n < 0 || first + n > c->ncb || (n > 0 && !in)) return fail(c, QK_EINVAL, "write_cbits: bad range");
+    for (int a = 0; a < n; ++a)
+        if (in[a] > 1) return fail(c, QK_EINVAL, "write_cbits: values must be 0 or 1");
+    qk_status s = flush(c);
+    if (s != QK_OK) return s;
+    if (n > 0) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->d_cbits + first, in, n, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the host buffer may be pageable
+    }
+    return QK_OK;
+}
+
+qk_status qk_get_state(qk_ctx *c, void *host_out, size_t bytes) {
+    if (!c) return QK_EINVAL;
+    if (c->n == 0 || !host_out || bytes != c->state_bytes)
+        return fail(c, QK_EINVAL, "get_state: need a buffer of exactly %zu bytes", c->state_bytes);
+    qk_status s = flush(c);
+    if (s == QK_OK) s = canonicalize(c);
+    if (s != QK_OK) return s;
+    CUDA_TRY(c, cudaMemcpyAsync(host_out, c->d_state, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return QK_OK;
+}
+
+qk_status qk_set_state(qk_ctx *c, const void *host_in, size_t bytes) {
+    if (!c) return QK_EINVAL;
+    if (c->n == 0 || !host_in || bytes != c->state_bytes)
+        return fail(c, QK_EINVAL, "set_state: need a buffer of exactly %zu bytes", c->state_bytes);
+    c->pending.clear();
+    for (int q = 0; q < c->n; ++q) c->l2p[q] = q;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_state, host_in, bytes, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return QK_OK;
+}
+
+qk_status qk_reset(qk_ctx *c) {
+    if (!c) return QK_EINVAL;
+    if (c->n == 0) return fail(c, QK_ESTATE, "reset: no qubits");
+    c->pending.clear();
+    for (int q = 0; q < c->n; ++q) c->l2p[q] = q;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_state, 0, c->state_bytes, c->stream));
+    CUDA_TRY(c, qk::launch_set_basis((int)c->prec, c->d_state, 0, c->stream));
+    return QK_OK;
+}
+
+qk_status qk_device_state(qk_ctx *c, void **dptr, size_t *bytes) {
+    if (!c) return QK_EINVAL;
+    if (!dptr || !bytes) return fail(c, QK_EINVAL, "device_state: null output");
+    qk_status s = flush(c);
+    if (s == QK_OK) s = canonicalize(c);
+    if (s != QK_OK) return s;
+    *dptr = c->d_state;
+    *bytes = c->state_bytes;
+    return QK_OK;
+}
+
+qk_status qk_flush(qk_ctx *c) {
+    if (!c) return QK_EINVAL;
+    return flush(c);
+}
+
+qk_status qk_sync(qk_ctx *c) {
+    if (!c) return QK_EINVAL;
+    qk_status s = flush(c);
+    if (s != QK_OK) return s;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return QK_OK;
+}
+
+int qk_num_qubits(const qk_ctx *c) { return c ? c->n : -1; }
+int qk_num_cbits(const qk_ctx *c) { return c ? c->ncb : -1; }
+
+qk_status qk_get_counters(const qk_ctx *c, uint64_t *launches, uint64_t *passes, uint64_t *bytes) {
+    if (!c) return QK_EINVAL;
+    if (launches) *launches = c->launches;
+    if (passes) *passes = c->passes_x1000 / 1000;
+    if (bytes) *bytes = (uint64_t)c->alg_bytes;
+    return QK_OK;
+}
+
+qk_status qk_reset_counters(qk_ctx *c) {
+    if (!c) return QK_EINVAL;
+    c->launches = 0;
+    c->passes_x1000 = 0;
+    c->alg_bytes = 0;
+    return QK_OK;
+}
+
+qk_status qk_profile(qk_ctx *c, uint64_t launches[QK_NUM_LAUNCH_CLASSES], double ms[QK_NUM_LAUNCH_CLASSES],
+                     double bytes[QK_NUM_LAUNCH_CLASSES]) {
+    if (!c) return QK_EINVAL;
+    if (!c->opt.profile) return fail(c, QK_ESTATE, "profile: context created without options.profile");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (auto &p : c->prof) {
+        float t = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&t, p.a, p.b));
+        c->prof_launches[p.cls]++;
+        c->prof_ms[p.cls] += t;
+        c->prof_bytes[p.cls] += p.bytes;
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    c->prof.clear();
+    for (int k = 0; k < QK_NUM_LAUNCH_CLASSES; ++k) {
+        if (launches) launches[k] = c->prof_launches[k];
+        if (ms) ms[k] = c->prof_ms[k];
+        if (bytes) bytes[k] = c->prof_bytes[k];
+        c->prof_launches[k] = 0;
+        c->prof_ms[k] = 0;
+        c->prof_bytes[k] = 0;
+    }
+    return QK_OK;
+}
+
+const char *qk_last_error(const qk_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// Internal declarations shared by the libqk host code and its CUDA kernels.
+// Nothing here is part of the public ABI (include/qk.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qk {
+
+constexpr int kMaxPos = 24;        // sorted bit positions a launch may insert
+constexpr int kMaxCond = 16;       // classical-condition cbits per gate
+constexpr int kMaxRphase = 62;     // cbits feeding one semiclassical phase
+constexpr int kMaxPermW = 30;      // permutation register width
+
+// Classical condition: the launch acts only if every listed cbit is 1.
+struct Cond {
+    int n;
+    int idx[kMaxCond];
+};
+
+// Sorted ascending bit positions, used to enumerate a subspace by inserting a
+// bit at each position into a dense counter.
+struct Positions {
+    int n;
+    int pos[kMaxPos];
+};
+
+// 2x2 update on target bit q where all control bits (cmask) are 1.
+struct U2Args {
+    double m[8];          // m00, m01, m10, m11 as (re, im) pairs, FP64 master
+    uint64_t cmask;
+    int q;
+    Positions ins;        // q and every control, sorted
+    uint64_t n_units;     // work units in the subspace
+    Cond cond;
+};
+
+// Multiply amplitudes whose index satisfies (i & mask) == val by f.
+struct PhaseArgs {
+    double f_re, f_im;
+    uint64_t mask, val;
+    Positions ins;        // bits of mask, sorted
+    uint64_t n_units;
+    Cond cond;
+    // semiclassical phase (rphase): when n_rphase > 0, f is computed on the
+    // device as exp(-2 pi i sum_l c[rphase_idx[l-1]] / 2^(l+1)).
+    int n_rphase;
+    int rphase_idx[kMaxRphase];
+};
+
+// Dense k-qubit matrix on arbitrary targets with controls.
+struct MatKArgs {
+    int k;
+    int tpos[8];          // physical bit of register bit (k-1-a), a = list index; tpos[0] = MSB
+    uint64_t cmask;
+    Positions ins;        // targets and controls, sorted
+    uint64_t n_groups;
+    const void *mat;      // device matrix, 2^k x 2^k, row-major, amplitude type
+    Cond cond;
+};
+
+// Controlled permutation of a w-bit register, out-of-place gather.
+struct PermArgs {
+    int w;
+    int rpos[kMaxPermW];  // physical bit of register list entry a (a = 0 is the MSB)
+    uint64_t cmask;
+    uint64_t n_amps;
+    int kind;             // 0 = mul-mod, 1 = table
+    uint64_t N, cinv, mu; // mul-mod: y -> cinv*y mod N for y < N, mu = floor((2^64-1)/N)
+    const uint32_t *finv; // table: inverse permutation
+    Cond cond;
+};
+
+// Device-side record of one single-qubit measurement decision.
+struct MeasSlot {
+    double p0;            // probability of reading 0
+    double scale;         // 1/sqrt(P_m)
+    int m;                // outcome
+    int pad;
+};
+
+// Qubit-relabelling gather: out[logical index] = in[physical index].
+struct RelabelArgs {
+    int n;
+    int phys_of[40];      // physical bit of logical qubit
+    uint64_t n_amps;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (kernels_basic.cu); prec: 0 = complex64, 1 = complex128
+// ---------------------------------------------------------------------------
+cudaError_t launch_u2(int prec, void *psi, const U2Args &a, const uint8_t *cbits, int n, int sms,
+                      cudaStream_t s);
+cudaError_t launch_phase(int prec, void *psi, const PhaseArgs &a, const uint8_t *cbits, int sms,
+                         cudaStream_t s);
+cudaError_t launch_matk(int prec, void *psi, const MatKArgs &a, const uint8_t *cbits, int sms,
+                        cudaStream_t s);
+cudaError_t launch_perm(int prec, const void *in, void *out, const PermArgs &a, const uint8_t *cbits,
+                        int sms, cudaStream_t s);
+cudaError_t launch_measure_reduce(int prec, const void *psi, int n, int q, double *partials,
+                                  int nblocks, cudaStream_t s);
+cudaError_t launch_measure_decide(const double *partials, int nblocks, double u, MeasSlot *slot,
+                                  uint8_t *cbits, int dest, cudaStream_t s);
+cudaError_t launch_measure_collapse(int prec, void *psi, int n, int q, const MeasSlot *slot, int sms,
+                                    cudaStream_t s);
+cudaError_t launch_set_basis(int prec, void *psi, uint64_t index, cudaStream_t s);
+cudaError_t launch_relabel(int prec, const void *in, void *out, const RelabelArgs &a, int sms,
+                           cudaStream_t s);
+
+}  // namespace qk

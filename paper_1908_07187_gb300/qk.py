@@ -1,0 +1,312 @@
+"""Thin ctypes binding of libqk (include/qk.h) -- argument marshalling only.
+
+Every operation on amplitudes runs in libqk's CUDA kernels.  If the shared
+library has not been built, importing this module raises: there is no CPU
+fallback.  Build it with ``python -m paper_1908_07187_gb300.build``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Dict, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqk.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libqk.so is not built ({LIB_PATH}); run python -m paper_1908_07187_gb300.build")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+QK_OK, QK_EINVAL, QK_ENOMEM, QK_EBUDGET, QK_ENOTBIJECTIVE, QK_ENOTUNITARY, QK_ECUDA, QK_ETIMEOUT, QK_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6, -7, -8
+QK_C64, QK_C128 = 0, 1
+QK_EXEC_PLAIN, QK_EXEC_FUSED = 0, 1
+NUM_LAUNCH_CLASSES = 7
+LAUNCH_CLASSES = ("tile", "u2", "phase", "block", "perm", "measure", "other")
+
+GATE = {
+    "x": -1, "y": -2, "z": -3, "h": -4, "s": -5, "sdg": -6, "t": -7, "tdg": -8,
+    "u3": -9, "p": -10, "rz": -11, "swap": -12,
+}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("exec_mode", ctypes.c_int), ("tile_qubits", ctypes.c_int), ("max_pending", ctypes.c_int),
+                ("profile", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("reserved", ctypes.c_int * 8)]
+
+
+_P = ctypes.c_void_p
+_IP = ctypes.POINTER(ctypes.c_int)
+_DP = ctypes.POINTER(ctypes.c_double)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+_U8P = ctypes.POINTER(ctypes.c_uint8)
+
+_SIGS = {
+    "qk_create": ([ctypes.POINTER(_P), ctypes.c_int, _P, ctypes.POINTER(Options)], ctypes.c_int),
+    "qk_destroy": ([_P], ctypes.c_int),
+    "qk_add_qubits": ([_P, ctypes.c_int, _IP], ctypes.c_int),
+    "qk_add_cbits": ([_P, ctypes.c_int, _IP], ctypes.c_int),
+    "qk_define_gate_matrix": ([_P, ctypes.c_int, _DP, ctypes.c_double, _IP], ctypes.c_int),
+    "qk_define_gate_perm_mulmod": ([_P, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _IP], ctypes.c_int),
+    "qk_define_gate_perm_table": ([_P, ctypes.c_int, _U64P, _IP], ctypes.c_int),
+    "qk_apply_gate": ([_P, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int, _DP,
+                       ctypes.c_int], ctypes.c_int),
+    "qk_apply_rphase_cbits": ([_P, ctypes.c_int, _IP, ctypes.c_int], ctypes.c_int),
+    "qk_measure": ([_P, _IP, ctypes.c_int, _DP, _IP, _U64P], ctypes.c_int),
+    "qk_read_cbits": ([_P, _U8P, ctypes.c_int], ctypes.c_int),
+    "qk_write_cbits": ([_P, ctypes.c_int, _U8P, ctypes.c_int], ctypes.c_int),
+    "qk_get_state": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
+    "qk_set_state": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
+    "qk_reset": ([_P], ctypes.c_int),
+    "qk_device_state": ([_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "qk_flush": ([_P], ctypes.c_int),
+    "qk_sync": ([_P], ctypes.c_int),
+    "qk_num_qubits": ([_P], ctypes.c_int),
+    "qk_num_cbits": ([_P], ctypes.c_int),
+    "qk_get_counters": ([_P, _U64P, _U64P, _U64P], ctypes.c_int),
+    "qk_reset_counters": ([_P], ctypes.c_int),
+    "qk_profile": ([_P, _U64P, _DP, _DP], ctypes.c_int),
+    "qk_last_error": ([_P], ctypes.c_char_p),
+    "qk_status_str": ([ctypes.c_int], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def exported_symbols():
+    """Names of the C entry points this binding uses (all declared in include/qk.h)."""
+    return list(_SIGS)
+
+
+class QKError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.qk_status_str(status).decode()}: {msg}")
+        self.status = status
+
+
+def _ints(xs: Optional[Sequence[int]]):
+    xs = list(xs or [])
+    return (ctypes.c_int * max(1, len(xs)))(*xs), len(xs)
+
+
+class Context:
+    """One libqk context: a state vector on the current CUDA device."""
+
+    def __init__(self, precision: str = "c64", exec_mode: str = "fused", stream: Optional[int] = None,
+                 tile_qubits: int = 0, profile: bool = False, hbm_budget_bytes: int = 0, max_pending: int = 0):
+        opt = Options()
+        opt.exec_mode = QK_EXEC_FUSED if exec_mode == "fused" else QK_EXEC_PLAIN
+        if exec_mode not in ("fused", "plain"):
+            raise ValueError("exec_mode must be 'fused' or 'plain'")
+        opt.tile_qubits = tile_qubits
+        opt.max_pending = max_pending
+        opt.profile = 1 if profile else 0
+        opt.hbm_budget_bytes = hbm_budget_bytes
+        self.precision = precision
+        self.cdtype = np.complex64 if precision == "c64" else np.complex128
+        prec = QK_C64 if precision == "c64" else QK_C128
+        if precision not in ("c64", "c128"):
+            raise ValueError("precision must be 'c64' or 'c128'")
+        h = _P()
+        st = _lib.qk_create(ctypes.byref(h), prec, _P(stream) if stream else None, ctypes.byref(opt))
+        if st != QK_OK:
+            raise QKError(st, "qk_create failed")
+        self._h = h
+        self._perm_cache: Dict[Tuple, int] = {}
+        self._mat_cache: Dict[bytes, int] = {}
+
+    # -- plumbing -------------------------------------------------------------
+    def _check(self, st: int):
+        if st != QK_OK:
+            raise QKError(st, _lib.qk_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.qk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def n_qubits(self) -> int:
+        return _lib.qk_num_qubits(self._h)
+
+    @property
+    def n_cbits(self) -> int:
+        return _lib.qk_num_cbits(self._h)
+
+    # -- the paper's commands ------------------------------------------------------
+    def add_qubits(self, n: int) -> int:
+        first = ctypes.c_int(0)
+        self._check(_lib.qk_add_qubits(self._h, n, ctypes.byref(first)))
+        return first.value
+
+    def add_cbits(self, n: int) -> int:
+        first = ctypes.c_int(0)
+        self._check(_lib.qk_add_cbits(self._h, n, ctypes.byref(first)))
+        return first.value
+
+    def define_gate_matrix(self, u, tol: float = 1e-9) -> int:
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.complex128))
+        k = int(round(np.log2(u.shape[0])))
+        if u.shape != (1 << k, 1 << k):
+            raise ValueError("matrix must be 2^k x 2^k")
+        flat = np.ascontiguousarray(u.view(np.float64).reshape(-1))
+        gid = ctypes.c_int(0)
+        self._check(_lib.qk_define_gate_matrix(self._h, k, flat.ctypes.data_as(_DP), tol, ctypes.byref(gid)))
+        return gid.value
+
+    def define_gate_perm_mulmod(self, w: int, c: int, N: int) -> int:
+        key = ("mulmod", w, c, N)
+        if key not in self._perm_cache:
+            gid = ctypes.c_int(0)
+            self._check(_lib.qk_define_gate_perm_mulmod(self._h, w, c, N, ctypes.byref(gid)))
+            self._perm_cache[key] = gid.value
+        return self._perm_cache[key]
+
+    def define_gate_perm_table(self, f) -> int:
+        f = np.ascontiguousarray(np.asarray(f, dtype=np.uint64))
+        w = int(round(np.log2(len(f))))
+        gid = ctypes.c_int(0)
+        self._check(_lib.qk_define_gate_perm_table(self._h, w, f.ctypes.data_as(_U64P), ctypes.byref(gid)))
+        return gid.value
+
+    def apply_gate(self, gate, targets: Sequence[int], controls: Sequence[int] = (), cond: Sequence[int] = (),
+                   params: Sequence[float] = ()):
+        gid = GATE[gate] if isinstance(gate, str) else int(gate)
+        t, nt = _ints(targets)
+        c, nc = _ints(controls)
+        k, nk = _ints(cond)
+        p = (ctypes.c_double * max(1, len(params)))(*params)
+        self._check(_lib.qk_apply_gate(self._h, gid, t, nt, c, nc, k, nk, p, len(params)))
+
+    def apply_rphase_cbits(self, target: int, cbits: Sequence[int]):
+        cb, n = _ints(cbits)
+        self._check(_lib.qk_apply_rphase_cbits(self._h, target, cb, n))
+
+    def measure(self, qubits: Sequence[int], uniforms: Sequence[float], dest: Optional[Sequence[int]] = None,
+                wait: bool = True) -> Optional[int]:
+        q, nq = _ints(qubits)
+        u = (ctypes.c_double * max(1, nq))(*uniforms)
+        d = _ints(dest)[0] if dest else None
+        out = ctypes.c_uint64(0)
+        self._check(_lib.qk_measure(self._h, q, nq, u, d, ctypes.byref(out) if wait else None))
+        return out.value if wait else None
+
+    def read_cbits(self, n: Optional[int] = None) -> np.ndarray:
+        n = self.n_cbits if n is None else n
+        buf = np.zeros(max(1, n), dtype=np.uint8)
+        self._check(_lib.qk_read_cbits(self._h, buf.ctypes.data_as(_U8P), n))
+        return buf[:n]
+
+    def write_cbits(self, first: int, values: Sequence[int]):
+        v = np.ascontiguousarray(np.asarray(values, dtype=np.uint8))
+        self._check(_lib.qk_write_cbits(self._h, first, v.ctypes.data_as(_U8P), len(v)))
+
+    def get_state(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        n = self.n_qubits
+        if out is None:
+            out = np.empty(1 << n, dtype=self.cdtype)
+        self._check(_lib.qk_get_state(self._h, out.ctypes.data, out.nbytes))
+        return out
+
+    def set_state(self, psi: np.ndarray):
+        psi = np.ascontiguousarray(np.asarray(psi, dtype=self.cdtype))
+        self._check(_lib.qk_set_state(self._h, psi.ctypes.data, psi.nbytes))
+
+    def reset(self):
+        self._check(_lib.qk_reset(self._h))
+
+    def device_state(self) -> Tuple[int, int]:
+        p = _P()
+        nb = ctypes.c_size_t(0)
+        self._check(_lib.qk_device_state(self._h, ctypes.byref(p), ctypes.byref(nb)))
+        return p.value, nb.value
+
+    def torch_view(self):
+        """The device state as a torch tensor (no copy, logical qubit order)."""
+        import torch
+
+        ptr, nb = self.device_state()
+        elem = 8 if self.precision == "c64" else 16
+
+        class _Arr:
+            __cuda_array_interface__ = {
+                "shape": (nb // elem,), "typestr": "<c8" if elem == 8 else "<c16",
+                "data": (ptr, False), "version": 3, "strides": None,
+            }
+        return torch.as_tensor(_Arr(), device="cuda")
+
+    def flush(self):
+        self._check(_lib.qk_flush(self._h))
+
+    def sync(self):
+        self._check(_lib.qk_sync(self._h))
+
+    def counters(self) -> Dict[str, int]:
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(_lib.qk_get_counters(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"launches": a.value, "state_passes": b.value, "algorithmic_bytes": c.value}
+
+    def reset_counters(self):
+        self._check(_lib.qk_reset_counters(self._h))
+
+    def profile(self) -> Dict[str, Dict[str, float]]:
+        L = (ctypes.c_uint64 * NUM_LAUNCH_CLASSES)()
+        M = (ctypes.c_double * NUM_LAUNCH_CLASSES)()
+        B = (ctypes.c_double * NUM_LAUNCH_CLASSES)()
+        self._check(_lib.qk_profile(self._h, L, M, B))
+        return {LAUNCH_CLASSES[k]: {"launches": int(L[k]), "ms": M[k], "bytes": B[k]}
+                for k in range(NUM_LAUNCH_CLASSES)}
+
+
+def run_ops(ctx: Context, ops) -> None:
+    """Marshal a sequence of workloads.Op into libqk calls (no arithmetic on
+    amplitudes here; measurements are enqueued without waiting)."""
+    for op in ops:
+        k = op.kind
+        if k == "measure":
+            ctx.measure(op.targets, op.uniforms, op.cbits or None, wait=False)
+        elif k == "mulmod":
+            a, j, N = (int(x) for x in op.params)
+            gid = ctx.define_gate_perm_mulmod(len(op.targets), pow(a, 1 << j, N), N)
+            ctx.apply_gate(gid, op.targets, op.controls, op.cond)
+        elif k == "rphase":
+            if op.cond:
+                raise ValueError("rphase takes no classical condition")
+            ctx.apply_rphase_cbits(op.targets[0], op.cbits)
+        elif k == "unitary":
+            key = bytes(np.asarray(op.params, dtype=np.float64).tobytes())
+            if key not in ctx._mat_cache:
+                v = np.asarray(op.params, dtype=np.float64)
+                d = int(round(np.sqrt(len(v) // 2)))
+                ctx._mat_cache[key] = ctx.define_gate_matrix((v[0::2] + 1j * v[1::2]).reshape(d, d))
+            ctx.apply_gate(ctx._mat_cache[key], op.targets, op.controls, op.cond)
+        else:
+            ctx.apply_gate(k, op.targets, op.controls, op.cond, op.params)
+
+
+def run_circuit(circ, precision: str = "c64", exec_mode: str = "fused", **kw) -> Context:
+    """Create a context for a workloads.Circuit and enqueue all of its ops."""
+    ctx = Context(precision, exec_mode, **kw)
+    ctx.add_qubits(circ.n_qubits)
+    if circ.n_cbits:
+        ctx.add_cbits(circ.n_cbits)
+    run_ops(ctx, circ.ops)
+    return ctx

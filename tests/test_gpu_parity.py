@@ -1,0 +1,280 @@
+"""GPU parity: libqk (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances: complex64 max |delta a| <= 1e-4 absolute and total-variation
+distance <= 1e-5 on the output distribution, complex128 <= 1e-12; permutations,
+measured bits and cbits bit-exact (a measured bit may differ only where the
+uniform lies within the precision's bound of P0, which the helper reports).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c64": 1e-4, "c128": 1e-12}
+TV_TOL = {"c64": 1e-5, "c128": 1e-12}
+MARGIN = {"c64": 1e-6, "c128": 1e-12}
+MODES = ("plain", "fused")
+
+
+@pytest.fixture(scope="module")
+def qk():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_07187_gb300 import qk as mod
+
+    return mod
+
+
+def tv(a, b):
+    return 0.5 * float(np.sum(np.abs(np.abs(a) ** 2 - np.abs(b) ** 2)))
+
+
+def check_state(got, ref, prec):
+    err = float(np.max(np.abs(got.astype(np.complex128) - ref)))
+    assert err <= TOL[prec], f"max |delta a| = {err:.3e}"
+    assert tv(got.astype(np.complex128), ref) <= TV_TOL[prec]
+
+
+def haar(d, rng):
+    z = (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) / math.sqrt(2)
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def new_ctx(qk, n, prec, mode, psi=None, ncb=0, **kw):
+    ctx = qk.Context(prec, mode, **kw)
+    ctx.add_qubits(n)
+    if ncb:
+        ctx.add_cbits(ncb)
+    if psi is not None:
+        ctx.set_state(psi)
+    return ctx
+
+
+# -- single gates on random states ---------------------------------------------
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("n", [1, 2, 5, 11, 15])
+def test_one_qubit_gates_every_target(qk, prec, mode, n):
+    rng = np.random.default_rng(n)
+    psi = workloads.random_state(n, 40 + n)
+    ctx = new_ctx(qk, n, prec, mode, psi)
+    ref = oracle.OracleState(n, psi=psi)
+    for q in range(n):
+        th, ph, la = rng.uniform(0, 2 * math.pi, 3)
+        ctx.apply_gate("u3", [q], params=[th, ph, la])
+        ref.apply_matrix(oracle.u3(th, ph, la), [q])
+        g = ["h", "x", "y", "z", "s", "t", "sdg"][q % 7]
+        ctx.apply_gate(g, [q])
+        ref.apply_matrix(oracle.GATES_1Q[g], [q])
+    check_state(ctx.get_state(), ref.psi, prec)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("target,controls", [(0, [1]), (3, [0]), (1, [0, 4]), (7, [2, 5, 0]), (12, [13]),
+                                             (5, [12, 1])])
+def test_controlled_gates(qk, prec, mode, target, controls):
+    n = 14
+    rng = np.random.default_rng(target * 17 + len(controls))
+    psi = workloads.random_state(n, 7)
+    U = haar(2, rng)
+    gid_ctx = new_ctx(qk, n, prec, mode, psi)
+    gid = gid_ctx.define_gate_matrix(U)
+    gid_ctx.apply_gate(gid, [target], controls)
+    gid_ctx.apply_gate("p", [target], controls, params=[0.37])
+    gid_ctx.apply_gate("x", [target], controls)
+    ref = oracle.OracleState(n, psi=psi)
+    ref.apply_matrix(U, [target], controls)
+    ref.apply_matrix(oracle.phase(0.37), [target], controls)
+    ref.apply_matrix(oracle.GATES_1Q["x"], [target], controls)
+    check_state(gid_ctx.get_state(), ref.psi, prec)
+    gid_ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("targets,controls", [((0, 1), ()), ((1, 0), ()), ((5, 2), (0,)), ((3, 9, 0), ()),
+                                              ((2, 7, 4, 11), (1,)), ((0, 1, 2, 3, 4), ()),
+                                              ((6, 1, 8, 3, 10, 0), ())])
+def test_k_qubit_matrix_gates(qk, prec, targets, controls):
+    n = 12
+    rng = np.random.default_rng(len(targets) * 5 + sum(targets))
+    U = haar(1 << len(targets), rng)
+    psi = workloads.random_state(n, 8)
+    ctx = new_ctx(qk, n, prec, "fused", psi)
+    gid = ctx.define_gate_matrix(U)
+    ctx.apply_gate(gid, targets, controls)
+    ref = oracle.OracleState(n, psi=psi)
+    ref.apply_matrix(U, targets, controls)
+    check_state(ctx.get_state(), ref.psi, prec)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_diagonal_k_qubit_gate_and_swap_relabel(qk, prec):
+    n = 9
+    psi = workloads.random_state(n, 12)
+    D = np.diag(np.exp(1j * np.array([0.0, 0.3, 0.0, -1.2])))
+    ctx = new_ctx(qk, n, prec, "fused", psi)
+    gid = ctx.define_gate_matrix(D)
+    ctx.apply_gate(gid, [4, 1])
+    ctx.apply_gate("swap", [0, 8])
+    ctx.apply_gate("h", [0])
+    ctx.apply_gate("swap", [3, 0])
+    ctx.apply_gate("swap", [2, 6], controls=[5])
+    ctx.apply_gate("x", [8], controls=[3])
+    ref = oracle.OracleState(n, psi=psi)
+    ref.apply_matrix(D, [4, 1])
+    ref.apply_matrix(oracle.SWAP, [0, 8])
+    ref.apply_matrix(oracle.GATES_1Q["h"], [0])
+    ref.apply_matrix(oracle.SWAP, [3, 0])
+    ref.apply_matrix(oracle.SWAP, [2, 6], [5])
+    ref.apply_matrix(oracle.GATES_1Q["x"], [8], [3])
+    check_state(ctx.get_state(), ref.psi, prec)
+    ctx.close()
+
+
+# -- permutations --------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_mulmod_permutation_bit_exact(qk, prec):
+    n = 13
+    N, c = 187, 23  # 8-bit register, gcd(23, 187) = 1
+    reg = [9, 2, 4, 11, 1, 7, 12, 5]
+    psi = workloads.random_state(n, 14)
+    ctx = new_ctx(qk, n, prec, "fused", psi)
+    gid = ctx.define_gate_perm_mulmod(8, c, N)
+    ctx.apply_gate(gid, reg, [3])
+    got = ctx.get_state()
+    ref = oracle.OracleState(n, psi=psi.astype(np.complex64 if prec == "c64" else np.complex128))
+    ref.apply_mulmod(c, N, reg, [3])
+    # a permutation moves amplitudes without arithmetic: bit-exact
+    assert np.array_equal(got, ref.psi.astype(got.dtype))
+    ctx.close()
+
+
+def test_perm_table_and_rejections(qk):
+    n = 6
+    rng = np.random.default_rng(3)
+    f = rng.permutation(16).astype(np.uint64)
+    psi = workloads.random_state(n, 15)
+    ctx = new_ctx(qk, n, "c128", "fused", psi)
+    gid = ctx.define_gate_perm_table(f)
+    ctx.apply_gate(gid, [5, 0, 3, 2])
+    ref = oracle.OracleState(n, psi=psi)
+    ref.apply_perm(f, [5, 0, 3, 2])
+    assert np.array_equal(ctx.get_state(), ref.psi)
+    with pytest.raises(qk.QKError) as e:
+        ctx.define_gate_perm_table([0, 0, 1, 2])
+    assert e.value.status == qk.QK_ENOTBIJECTIVE
+    with pytest.raises(qk.QKError) as e:
+        ctx.define_gate_perm_mulmod(4, 5, 15)
+    assert e.value.status == qk.QK_ENOTBIJECTIVE
+    with pytest.raises(qk.QKError) as e:
+        ctx.apply_gate("h", [6])
+    assert e.value.status == qk.QK_EINVAL
+    with pytest.raises(qk.QKError):
+        ctx.define_gate_matrix(np.array([[1, 1], [0, 1]]))
+    ctx.close()
+
+
+# -- measurement and classical control ---------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("mode", MODES)
+def test_measurement_bits_and_collapse(qk, prec, mode):
+    n = 12
+    psi = workloads.random_state(n, 16)
+    rng = workloads.SplitMix64(99)
+    qubits = [0, 5, 11, 3, 7]
+    us = [rng.uniform() for _ in qubits]
+    ctx = new_ctx(qk, n, prec, mode, psi, ncb=len(qubits))
+    v = ctx.measure(qubits, us, list(range(len(qubits))))
+    ref = oracle.OracleState(n, len(qubits), psi=psi)
+    rv = ref.measure(qubits, us, list(range(len(qubits))))
+    margins = [abs(u - p) for u, p in zip(us, ref.last_p0)]
+    if min(margins) > MARGIN[prec]:
+        assert v == rv
+        assert list(ctx.read_cbits()) == list(ref.cbits)
+        check_state(ctx.get_state(), ref.psi, prec)
+    ctx.close()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_classical_condition_and_rphase(qk, mode):
+    n = 7
+    psi = workloads.random_state(n, 17)
+    ctx = new_ctx(qk, n, "c128", mode, psi, ncb=4)
+    ref = oracle.OracleState(n, 4, psi=psi)
+    ctx.write_cbits(0, [1, 0, 1, 1])
+    ref.cbits[:] = [1, 0, 1, 1]
+    ctx.apply_gate("x", [2], cond=[0])          # acts
+    ctx.apply_gate("h", [4], cond=[0, 1])       # does not act
+    ctx.apply_gate("u3", [6], controls=[1], cond=[2, 3], params=[0.3, 0.2, 0.1])
+    ctx.apply_rphase_cbits(0, [0, 1, 2, 3])
+    ctx.apply_rphase_cbits(5, [3])
+    ref.apply_matrix(oracle.GATES_1Q["x"], [2])
+    ref.apply_matrix(oracle.u3(0.3, 0.2, 0.1), [6], [1])
+    ref.rphase(0, [0, 1, 2, 3])
+    ref.rphase(5, [3])
+    check_state(ctx.get_state(), ref.psi, "c128")
+    ctx.close()
+
+
+# -- whole workloads --------------------------------------------------------------------------
+
+def test_plain_c128_12q_circuit(qk):
+    circ = workloads.plain_c128_circuit(seed=1)
+    ref = oracle.run_circuit(circ)
+    for mode in MODES:
+        ctx = qk.run_circuit(circ, "c128", mode)
+        bits = ctx.read_cbits()
+        got = ctx.get_state()
+        assert list(bits) == list(ref.cbits)
+        check_state(got, ref.psi, "c128")
+        ctx.close()
+
+
+@pytest.mark.parametrize("n", [10, 14, 17])
+@pytest.mark.parametrize("mode", MODES)
+def test_layered_circuit_c64(qk, n, mode):
+    circ = workloads.layered_circuit(n, seed=2, n_gates=500)
+    ref = oracle.run_circuit(circ)
+    ctx = qk.run_circuit(circ, "c64", mode)
+    check_state(ctx.get_state(), ref.psi, "c64")
+    ctx.close()
+
+
+@pytest.mark.parametrize("b", [4, 6, 12])
+def test_kitaev_order_finding_bits_exact(qk, b):
+    N, a = (15, 7) if b == 4 else workloads.kitaev_parameters(b, seed=3)
+    circ = workloads.kitaev_circuit(N, a, seed=5)
+    ref = oracle.run_circuit(circ)
+    for mode in MODES:
+        ctx = qk.run_circuit(circ, "c64", mode)
+        assert list(ctx.read_cbits()) == [int(x) for x in ref.cbits], mode
+        check_state(ctx.get_state(), ref.psi, "c64")
+        ctx.close()
+
+
+def test_add_qubits_keeps_state_and_counters(qk):
+    psi = workloads.random_state(5, 19)
+    ctx = new_ctx(qk, 5, "c64", "plain", psi)
+    ctx.reset_counters()
+    ctx.apply_gate("h", [2])
+    assert ctx.counters()["launches"] == 1
+    ctx.add_qubits(3)
+    ref = oracle.OracleState(5, psi=psi)
+    ref.apply_matrix(oracle.GATES_1Q["h"], [2])
+    ref.add_qubits(3)
+    check_state(ctx.get_state(), ref.psi, "c64")
+    ctx.close()

@@ -1,0 +1,373 @@
+"""Benchmark: 30-qubit layered-circuit throughput (gates/s) and HBM roofline.
+
+One step = one pass of the hot path over the single-large-state workload:
+|0...0> initialisation of the 2^n complex64 state, 500 gates of alternating
+U3-on-every-qubit / CZ-even / CZ-odd layers (seeded angles), the paper's QFT
+command sequence on all n qubits (H, CPHASE pi/2^(i+1), SWAPs), then sampling the
+output by measuring all n qubits in order with seeded uniforms (the outcome is
+read back).  gates/s counts the 500 + QFT gate commands (980 at n = 30).
+
+JSON line keys follow the harness contract; ``value`` is timed on the device with
+CUDA events on the engine's stream, ``e2e`` through the public API from the host
+(gate descriptors in, measured outcome out), ``roofline`` for the kernel class with
+the largest share of device time, ``cpu_baseline`` the complex128 CPU oracle on a
+bounded sample of the same circuit.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--n 30] [--mode fused|plain]
+       python bench.py --impl reference ...   (the CPU oracle arm)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "30-qubit gates/s & % HBM peak; served circuits/s + p99 vs plain, TV err<=1e-5"
+UNIT = "gates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--mode", default="fused", choices=["fused", "plain"])
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-pass-per-gate comparison")
+    return ap.parse_args()
+
+
+def workload(n: int, seed: int):
+    return workloads.layered_circuit(n, seed=seed, n_gates=500, qft=True, measure=n)
+
+
+def gate_ops(circ):
+    return [op for op in circ.ops if op.kind != "measure"]
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1908_07187_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_class: str, n: int):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        rec = d.get(f"{kernel_class}_n{n}")
+        if rec and rec.get("src_sha") == kernel_source_sha():
+            return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_state(n: int, circ):
+    """An n-qubit oracle state (every page touched) with the workload's first gate
+    applied, untimed."""
+    import oracle
+
+    st = oracle.OracleState(n)
+    st.psi.fill(0)          # touch every page before timing
+    st.psi[0] = 1
+    st.apply_op(gate_ops(circ)[0])
+    return st
+
+
+def oracle_gates_per_s(st, circ, first: int, count: int):
+    """Time the complex128 oracle, as it stands (one thread), on gate ops
+    first..first+count-1 of the workload.  Returns gates/s."""
+    ops = gate_ops(circ)
+    t0 = time.perf_counter()
+    for op in ops[first:first + count]:
+        st.apply_op(op)
+    return count / (time.perf_counter() - t0)
+
+
+def host_mem_gib():
+    try:
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable"):
+                    return int(line.split()[1]) / 2 ** 20
+    except Exception:
+        pass
+    return 0.0
+
+
+def oracle_size(n: int):
+    """Largest qubit count <= n whose complex128 state fits comfortably in host RAM."""
+    m = n
+    while m > 20 and host_mem_gib() < (16 << m) / 2 ** 30 * 1.3:
+        m -= 1
+    return m
+
+
+def cpu_baseline(n: int, circ, count: int = 1):
+    m = oracle_size(n)
+    c = circ if m == n else workload(m, 2)
+    st = oracle_state(m, c)
+    gps = oracle_gates_per_s(st, c, 1, count) * 2.0 ** (m - n)   # per-gate cost scales with 2^n
+    sample = f"gates 2..{count + 1} of the {m}-qubit layered circuit on the complex128 oracle, 1 thread"
+    if m != n:
+        sample += f", scaled by 2^{m - n} to {n} qubits"
+    return {"value": gps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = args.n
+    m = oracle_size(min(n, 27))   # one step stays near a second of CPU time
+    circ = workload(m, 2)
+    st = oracle_state(m, circ)
+    per_step = 1
+    vals = []
+    pos = 1
+    for s in range(args.warmup + args.steps):
+        gps = oracle_gates_per_s(st, circ, pos, per_step) * 2.0 ** (m - n)
+        pos += per_step
+        if s >= args.warmup:
+            vals.append(gps)
+    value = statistics.median(vals)
+    sample = f"{per_step} gate per step of the {m}-qubit layered circuit on the complex128 oracle, 1 thread"
+    if m != n:
+        sample += f", scaled by 2^{m - n} to {n} qubits"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * per_step / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": f"layered U3/CZ-brickwork 500 gates + QFT({n}) + measure all, {n} qubits",
+                       "n_qubits": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1908_07187_gb300 import qk
+
+    n = args.n
+    circ = workload(n, 2 + rank)          # independent replica per rank
+    gops = gate_ops(circ)
+    meas = [op for op in circ.ops if op.kind == "measure"]
+    n_gates = len(gops)
+    stream = torch.cuda.Stream()
+    ctx = qk.Context("c64", args.mode, stream=stream.cuda_stream, profile=True)
+    ctx.add_qubits(n)
+    ctx.add_cbits(n)
+
+    def step():
+        ctx.reset()
+        qk.run_ops(ctx, gops)
+        for op in meas:
+            ctx.measure(op.targets, op.uniforms, op.cbits, wait=False)
+        ctx.flush()
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+    ctx.profile()                      # drop warm-up launch records
+    ctx.reset_counters()
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    counters = ctx.counters()
+    prof = ctx.profile()
+    if dist:
+        dist.barrier()
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * n_gates * args.steps / (ms / 1000.0)
+
+    # end to end through the public API: host gate descriptors in, outcome out
+    h2d = 0
+    for op in gops:
+        h2d += 4 * (len(op.targets) + len(op.controls) + len(op.cond)) + 8 * len(op.params)
+    for op in meas:
+        h2d += 4 * (len(op.targets) + len(op.cbits)) + 8 * len(op.uniforms)
+    d2h = 8
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.reset()
+        qk.run_ops(ctx, gops)
+        for op in meas:
+            outcome = ctx.measure(op.targets, op.uniforms, op.cbits, wait=True)
+    t_e2e = time.perf_counter() - t0
+    e2e_value = world * n_gates * e2e_steps / t_e2e
+    _ = outcome
+
+    # one-pass-per-gate comparison (fused vs plain), a short run
+    plain = None
+    if args.mode == "fused" and not args.no_plain:
+        pctx = qk.Context("c64", "plain", stream=stream.cuda_stream)
+        pctx.add_qubits(n)
+        pctx.add_cbits(n)
+        qk.run_ops(pctx, gops)  # warm
+        pctx.sync()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        pctx.reset()
+        qk.run_ops(pctx, gops)
+        for op in meas:
+            pctx.measure(op.targets, op.uniforms, op.cbits, wait=False)
+        pctx.flush()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1)
+        plain = {"value": n_gates / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms}
+        pctx.close()
+
+    # roofline for the kernel class with the largest device-time share
+    top = max(prof, key=lambda k: prof[k]["ms"])
+    rec = prof[top]
+    peak, peak_kind = peaks()
+    achieved = (rec["bytes"] / rec["launches"]) / (rec["ms"] / rec["launches"] / 1000.0) / 1e9 if rec["launches"] else 0
+    traffic = recorded_traffic(top, n)
+    tot_ms = sum(v["ms"] for v in prof.values())
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": top,
+                "peak_kind": peak_kind, "launches_per_step": rec["launches"] / args.steps,
+                "share_of_device_time": round(rec["ms"] / tot_ms, 4) if tot_ms else None,
+                "alg_bytes_per_launch": rec["bytes"] / rec["launches"] if rec["launches"] else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(n, circ)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": f"layered U3/CZ-brickwork 500 gates + QFT({n}) + measure all, {n} qubits complex64",
+                       "n_qubits": n, "gates_per_step": n_gates, "mode": args.mode,
+                       "l2": "state (%.1f GiB) larger than L2" % ((8 << n) / 2 ** 30), "parallelism": f"replicas{world}"},
+            "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": counters["launches"],
+            "state_passes_per_step": counters["state_passes"] / args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "plain_path": plain,
+            "launch_profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items() if v["launches"]},
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

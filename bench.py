@@ -183,7 +183,7 @@ def cpu_baseline(n: int, circ, count: int = 1):
     c = circ if m == n else workload(m, 2)
     st = oracle_state(m, c)
     gps = oracle_gates_per_s(st, c, 1, count) * 2.0 ** (m - n)   # per-gate cost scales with 2^n
-    sample = f"gates 2..{count + 1} of the {m}-qubit layered circuit on the complex128 oracle, 1 thread"
+    sample = f"gate ops 2..{count + 1} of the {m}-qubit layered circuit (gate 1 untimed) on the complex128 oracle, 1 thread"
     if m != n:
         sample += f", scaled by 2^{m - n} to {n} qubits"
     return {"value": gps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}

@@ -129,6 +129,32 @@ qk_status qk_define_gate_matrix(qk_ctx *ctx, int k, const double *u, double unit
  * (QK_ENOTBIJECTIVE otherwise).  Index arithmetic is exact (64-bit). */
 qk_status qk_define_gate_perm_mulmod(qk_ctx *ctx, int w, uint64_t c, uint64_t N, int *gate_id);
 
+/* Allocation-free variant of the mul-mod permutation gate.  The paper has no
+ * counterpart: it exists for callers that cannot allocate device memory --
+ * latency-critical loops where an allocation's implicit device synchronisation
+ * would stall every other stream, host applications whose own memory manager
+ * owns all device memory, and embedded users that must stay inside a device
+ * memory budget reserved up front.
+ * Applies x -> c*x mod N (x < N; x >= N unchanged) to the w-qubit register
+ * targets[0..w-1] (first-listed = MSB) of the caller's device state d_state
+ * (2^n amplitudes, interleaved (re, im), complex64 or complex128, 16-byte
+ * aligned, qubit q = index bit q) wherever every control qubit is |1>.  The work
+ * is enqueued on cuda_stream (NULL = the legacy default stream) and the call
+ * returns without waiting.  Requires gcd(c, N) = 1, c < N, 2 <= N <= 2^w.
+ * No device memory is allocated: the gather goes through one fixed scratch
+ * array of QK_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the library
+ * holds until the process exits, so states above that size (complex64 above 21
+ * qubits, complex128 above 20) are rejected with QK_EBUDGET.  The first call on
+ * each device looks up the array's device address with that device current;
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls whose GPU work may overlap (different streams or threads without
+ * ordering between them) race and corrupt each other's results.
+ * Errors: QK_EINVAL (bad pointer, alignment, qubit lists, N or c),
+ * QK_ENOTBIJECTIVE (gcd(c, N) != 1), QK_EBUDGET (state too large), QK_ECUDA. */
+#define QK_NOALLOC_SCRATCH_BYTES (16u << 20)
+qk_status qk_apply_perm_mulmod_noalloc(void *d_state, int n, qk_precision precision, const int *targets, int w,
+                                       const int *controls, int nc, uint64_t c, uint64_t N, void *cuda_stream);
+
 /* Define a gate as an arbitrary function f on a w-qubit register value (1..24):
  * f is 2^w entries, copied, and must be a bijection (QK_ENOTBIJECTIVE). */
 qk_status qk_define_gate_perm_table(qk_ctx *ctx, int w, const uint64_t *f, int *gate_id);

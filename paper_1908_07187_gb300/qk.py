@@ -53,6 +53,8 @@ _SIGS = {
     "qk_define_gate_matrix": ([_P, ctypes.c_int, _DP, ctypes.c_double, _IP], ctypes.c_int),
     "qk_define_gate_perm_mulmod": ([_P, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, _IP], ctypes.c_int),
     "qk_define_gate_perm_table": ([_P, ctypes.c_int, _U64P, _IP], ctypes.c_int),
+    "qk_apply_perm_mulmod_noalloc": ([_P, ctypes.c_int, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int,
+                                      ctypes.c_uint64, ctypes.c_uint64, _P], ctypes.c_int),
     "qk_apply_gate": ([_P, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int, _DP,
                        ctypes.c_int], ctypes.c_int),
     "qk_apply_rphase_cbits": ([_P, ctypes.c_int, _IP, ctypes.c_int], ctypes.c_int),

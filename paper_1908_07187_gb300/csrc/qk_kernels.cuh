@@ -87,6 +87,51 @@ struct RelabelArgs {
 };
 
 // ---------------------------------------------------------------------------
+// fused tile pass (K3), complex64.  A tile is 2^13 amplitudes over 13 physical
+// qubits S[0..12] (S[b] = b for b < 5, so 32 consecutive amplitudes form the
+// lane dimension of every global access).  256 threads hold 32 amplitudes each
+// in registers; three fixed "arrangements" say which local bits are register,
+// lane and warp bits:
+//   ARR_IO: lanes = local 0..4, registers = local 5..9,  warps = local 10..12
+//   ARR_LO: registers = local 0..4, lanes = local 5..9,  warps = local 10..12
+//   ARR_HI: lanes = local 0..4, registers = local 8..12, warps = local 5..7
+// Gates act on register bits only; switching arrangement is a transpose through
+// shared memory.  Loads use ARR_IO, stores use ARR_IO or ARR_HI.
+// ---------------------------------------------------------------------------
+constexpr int kTileQubits = 13;
+constexpr int kTileThreads = 256;
+constexpr int kTileMaxOps = 400;
+constexpr int kTileMaxConds = 4;
+enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
+enum TileOpKind : uint8_t { TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2 };
+
+struct TileOp {
+    uint8_t kind;          // TileOpKind
+    uint8_t k;             // U2: target register bit; XPOSE: new arrangement
+    uint8_t rmask, rval;   // condition on register bits (5-bit register index space)
+    uint16_t tmask, tval;  // condition on thread bits: bits 0..4 lane, 5..7 warp
+    uint16_t cond;         // index into TileParams::conds, 0xffff = unconditional
+    uint16_t pad;
+    uint64_t gmask, gval;  // condition on the tile's fixed (non-tile) physical bits
+    float m[8];            // U2: m00, m01, m10, m11 as (re, im); PHASE: factor (re, im)
+};
+
+struct TileParams {
+    uint64_t n_tiles;
+    int n;
+    int nfix;
+    int8_t S[16];          // physical qubit of local bit b
+    int8_t fixed[40];      // physical bits of the tile index, ascending
+    int store_arr;
+    int n_conds;
+    Cond conds[kTileMaxConds];
+    int nops;
+    TileOp ops[kTileMaxOps];
+};
+
+cudaError_t launch_tile(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // launchers (kernels_basic.cu); prec: 0 = complex64, 1 = complex128
 // ---------------------------------------------------------------------------
 cudaError_t launch_u2(int prec, void *psi, const U2Args &a, const uint8_t *cbits, int n, int sms,

@@ -1,4 +1,17 @@
 // Planner for the fused mode: groups queued gates into tile passes (K3).
+//
+// Two gates commute when neither one's non-diagonal qubit (the target of a 2x2
+// gate) is touched by the other; diagonal gates and the control qubits of a
+// controlled gate act diagonally.  A pass picks a set S of 13 physical qubits
+// (always 0..4, for coalesced access) and takes, in order, every queued gate that
+//   - is diagonal, or is a 2x2 gate whose target is in S (controls may be
+//     anywhere: a control outside S is constant over a tile), and
+//   - commutes with every earlier gate the pass leaves behind.
+// Qubits join S greedily as 2x2 targets are met.  Inside the pass the taken
+// gates are list-scheduled over the three register arrangements of the tile
+// kernel, inserting a transpose when no ready gate fits the current one.
+#include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "qk_plan.h"
@@ -6,17 +19,267 @@
 namespace qk {
 
 struct TilePlanner {
-    int dummy = 0;
+    std::vector<int> scratch;
 };
 
 TilePlanner *make_planner() { return new TilePlanner(); }
 void free_planner(TilePlanner *p) { delete p; }
 
-qk_status run_fused(TilePlanner *p, qk_ctx *c, const std::vector<FusedOp> &ops) {
-    (void)p;
-    for (const auto &op : ops) {
-        qk_status s = ctx_run_plain(c, op);
-        if (s != QK_OK) return s;
+namespace {
+
+struct POp {
+    const FusedOp *op;
+    uint64_t nd;   // non-diagonal qubits
+    uint64_t all;  // every qubit the op depends on
+};
+
+POp classify(const FusedOp &op) {
+    POp p;
+    p.op = &op;
+    if (op.kind == FusedOp::U2) {
+        p.nd = 1ull << op.q;
+        p.all = p.nd | op.cmask;
+    } else {
+        p.nd = 0;
+        p.all = op.mask;
+    }
+    return p;
+}
+
+bool commute(const POp &a, const POp &b) { return !(a.nd & b.all) && !(b.nd & a.all); }
+
+bool same_cond(const Cond &a, const Cond &b) {
+    if (a.n != b.n) return false;
+    for (int k = 0; k < a.n; ++k)
+        if (a.idx[k] != b.idx[k]) return false;
+    return true;
+}
+
+// slot of a local bit in an arrangement: 0 = register, 1 = lane, 2 = warp; *pos = index
+int slot_of(int arr, int lb, int *pos) {
+    if (arr == ARR_IO) {
+        if (lb < 5) { *pos = lb; return 1; }
+        if (lb < 10) { *pos = lb - 5; return 0; }
+        *pos = lb - 10;
+        return 2;
+    }
+    if (arr == ARR_LO) {
+        if (lb < 5) { *pos = lb; return 0; }
+        if (lb < 10) { *pos = lb - 5; return 1; }
+        *pos = lb - 10;
+        return 2;
+    }
+    // ARR_HI
+    if (lb < 5) { *pos = lb; return 1; }
+    if (lb < 8) { *pos = lb - 5; return 2; }
+    *pos = lb - 8;
+    return 0;
+}
+
+bool executable(const POp &p, int arr, const int *local_of) {
+    if (p.op->kind != FusedOp::U2) return true;
+    int pos;
+    return slot_of(arr, local_of[p.op->q], &pos) == 0;
+}
+
+// Encode a mask/value condition over physical qubits into register / thread /
+// fixed-bit parts for an arrangement.
+void encode_cond(uint64_t mask, uint64_t val, int arr, const int *local_of, TileOp &t) {
+    t.rmask = t.rval = 0;
+    t.tmask = t.tval = 0;
+    t.gmask = t.gval = 0;
+    for (int b = 0; b < 64; ++b) {
+        if (!((mask >> b) & 1)) continue;
+        const int bit = (int)((val >> b) & 1);
+        const int lb = local_of[b];
+        if (lb < 0) {
+            t.gmask |= 1ull << b;
+            t.gval |= (uint64_t)bit << b;
+            continue;
+        }
+        int pos;
+        const int s = slot_of(arr, lb, &pos);
+        if (s == 0) {
+            t.rmask |= (uint8_t)(1 << pos);
+            t.rval |= (uint8_t)(bit << pos);
+        } else if (s == 1) {
+            t.tmask |= (uint16_t)(1 << pos);
+            t.tval |= (uint16_t)(bit << pos);
+        } else {
+            t.tmask |= (uint16_t)(1 << (5 + pos));
+            t.tval |= (uint16_t)(bit << (5 + pos));
+        }
+    }
+}
+
+}  // namespace
+
+qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> &ops) {
+    (void)planner;
+    const int n = ctx_n(c);
+    if (n < kTileQubits || ctx_prec(c) != 0) {
+        for (const auto &op : ops) {
+            qk_status s = ctx_run_plain(c, op);
+            if (s != QK_OK) return s;
+        }
+        return QK_OK;
+    }
+    std::vector<POp> rem;
+    rem.reserve(ops.size());
+    for (const auto &op : ops) rem.push_back(classify(op));
+
+    const int max_take = kTileMaxOps / 2 - 1;  // plus one transpose per gate at most, plus the last
+    std::vector<POp> left, taken;
+    while (!rem.empty()) {
+        // ---- choose S and the gates this pass takes
+        uint64_t S = (1ull << 5) - 1;
+        int cnt = 5;
+        uint64_t ndb = 0, allb = 0;
+        std::vector<Cond> conds;
+        left.clear();
+        taken.clear();
+        for (const POp &p : rem) {
+            bool ok = (int)taken.size() < max_take && !(p.nd & allb) && !(p.all & ndb);
+            if (ok && p.op->kind == FusedOp::U2) {
+                const uint64_t t = 1ull << p.op->q;
+                if (!(S & t)) {
+                    if (cnt < kTileQubits) {
+                        S |= t;
+                        ++cnt;
+                    } else {
+                        ok = false;
+                    }
+                }
+            }
+            if (ok && p.op->cond.n) {
+                bool found = false;
+                for (const auto &cd : conds) found = found || same_cond(cd, p.op->cond);
+                if (!found) {
+                    if ((int)conds.size() < kTileMaxConds) conds.push_back(p.op->cond);
+                    else ok = false;
+                }
+            }
+            if (ok) {
+                taken.push_back(p);
+            } else {
+                left.push_back(p);
+                ndb |= p.nd;
+                allb |= p.all;
+            }
+        }
+        // fill S up to 13 qubits with the lowest unused ones
+        for (int b = 5; b < n && cnt < kTileQubits; ++b)
+            if (!((S >> b) & 1)) {
+                S |= 1ull << b;
+                ++cnt;
+            }
+
+        static thread_local TileParams P;
+        std::memset(&P, 0, offsetof(TileParams, ops));
+        P.n = n;
+        P.n_tiles = 1ull << (n - kTileQubits);
+        int local_of[64];
+        for (int b = 0; b < 64; ++b) local_of[b] = -1;
+        {
+            int lb = 0, fb = 0;
+            for (int b = 0; b < n; ++b) {
+                if ((S >> b) & 1) {
+                    P.S[lb] = (int8_t)b;
+                    local_of[b] = lb++;
+                } else {
+                    P.fixed[fb++] = (int8_t)b;
+                }
+            }
+            P.nfix = fb;
+        }
+        P.n_conds = (int)conds.size();
+        for (int k = 0; k < P.n_conds; ++k) P.conds[k] = conds[k];
+
+        // ---- list-schedule the taken gates over the arrangements
+        const int m = (int)taken.size();
+        std::vector<int> npred(m, 0);
+        std::vector<std::vector<int>> succ(m);
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < j; ++i)
+                if (!commute(taken[i], taken[j])) {
+                    npred[j]++;
+                    succ[i].push_back(j);
+                }
+        std::vector<char> done(m, 0);
+        int ndone = 0, cur = ARR_IO, nops = 0;
+        auto emit = [&](int j, int arr) {
+            const FusedOp &op = *taken[j].op;
+            TileOp &t = P.ops[nops++];
+            std::memset(&t, 0, sizeof t);
+            t.cond = 0xffff;
+            if (op.cond.n)
+                for (int k = 0; k < P.n_conds; ++k)
+                    if (same_cond(P.conds[k], op.cond)) t.cond = (uint16_t)k;
+            if (op.kind == FusedOp::U2) {
+                t.kind = TOP_U2;
+                int pos;
+                slot_of(arr, local_of[op.q], &pos);
+                t.k = (uint8_t)pos;
+                encode_cond(op.cmask, op.cmask, arr, local_of, t);
+                for (int e = 0; e < 4; ++e) {
+                    t.m[2 * e] = (float)op.m[e].real();
+                    t.m[2 * e + 1] = (float)op.m[e].imag();
+                }
+            } else {
+                t.kind = TOP_PHASE;
+                encode_cond(op.mask, op.val, arr, local_of, t);
+                t.m[0] = (float)op.f.real();
+                t.m[1] = (float)op.f.imag();
+            }
+            done[j] = 1;
+            ++ndone;
+            for (int s : succ[j]) npred[s]--;
+        };
+        while (ndone < m) {
+            bool progress = false;
+            for (int j = 0; j < m; ++j)
+                if (!done[j] && npred[j] == 0 && executable(taken[j], cur, local_of)) {
+                    emit(j, cur);
+                    progress = true;
+                }
+            if (ndone == m) break;
+            if (!progress) {
+                int best = -1, best_cnt = -1;
+                for (int a = 0; a < 3; ++a) {
+                    if (a == cur) continue;
+                    int cntr = 0;
+                    for (int j = 0; j < m; ++j)
+                        if (!done[j] && npred[j] == 0 && executable(taken[j], a, local_of)) ++cntr;
+                    if (cntr > best_cnt) {
+                        best_cnt = cntr;
+                        best = a;
+                    }
+                }
+                TileOp &t = P.ops[nops++];
+                std::memset(&t, 0, sizeof t);
+                t.kind = TOP_XPOSE;
+                t.k = (uint8_t)best;
+                t.cond = 0xffff;
+                cur = best;
+            }
+        }
+        if (cur == ARR_LO) {
+            TileOp &t = P.ops[nops++];
+            std::memset(&t, 0, sizeof t);
+            t.kind = TOP_XPOSE;
+            t.k = ARR_IO;
+            t.cond = 0xffff;
+            cur = ARR_IO;
+        }
+        P.nops = nops;
+        P.store_arr = cur;
+
+        void *tok = nullptr;
+        ctx_launch_begin(c, 0, 2.0 * 8.0 * (double)(1ull << n), &tok);
+        cudaError_t e = launch_tile(ctx_state(c), P, ctx_cbits(c), ctx_stream(c));
+        ctx_launch_end(tok);
+        if (e != cudaSuccess) return ctx_fail(c, QK_ECUDA, cudaGetErrorString(e));
+        rem.swap(left);
     }
     return QK_OK;
 }

@@ -278,3 +278,69 @@ def test_add_qubits_keeps_state_and_counters(qk):
     ref.add_qubits(3)
     check_state(ctx.get_state(), ref.psi, "c64")
     ctx.close()
+
+
+# -- fused tile passes on random mixed circuits ------------------------------------------------
+
+def random_mixed_ops(n, n_ops, seed, ncb=0):
+    """Seeded random mix of 1-qubit gates with 0..2 controls, diagonal gates with
+    controls, SWAPs and classically conditioned gates."""
+    rng = np.random.default_rng(seed)
+    ops = []
+    kinds = ["u3", "h", "x", "y", "z", "s", "t", "p", "rz", "swap", "sdg"]
+    for _ in range(n_ops):
+        k = kinds[rng.integers(len(kinds))]
+        qs = [int(x) for x in rng.choice(n, size=4, replace=False)]
+        nc = int(rng.integers(0, 3))
+        cond = ()
+        if ncb and rng.random() < 0.15:
+            cond = (int(rng.integers(ncb)),)
+        if k == "swap":
+            ops.append(workloads.Op("swap", (qs[0], qs[1]), controls=tuple(qs[2:2 + (nc > 1)]), cond=cond))
+            continue
+        params = ()
+        if k == "u3":
+            params = tuple(float(x) for x in rng.uniform(0, 2 * math.pi, 3))
+        elif k in ("p", "rz"):
+            params = (float(rng.uniform(0, 2 * math.pi)),)
+        ops.append(workloads.Op(k, (qs[0],), controls=tuple(qs[1:1 + nc]), params=params, cond=cond))
+    return ops
+
+
+def oracle_apply(st, op):
+    if op.cond and not all(st.cbits[c] for c in op.cond):
+        return
+    if op.kind == "rz":
+        th = op.params[0]
+        U = np.diag([np.exp(-0.5j * th), np.exp(0.5j * th)])
+    else:
+        U = oracle.gate_matrix(op.kind, op.params)
+    st.apply_matrix(U, op.targets, op.controls)
+
+
+@pytest.mark.parametrize("n,seed", [(13, 1), (14, 2), (15, 3), (16, 4), (18, 5), (20, 6)])
+def test_fused_random_mixed_circuits(qk, n, seed):
+    ops = random_mixed_ops(n, 300, seed, ncb=3)
+    psi = workloads.random_state(n, 60 + seed)
+    ctx = new_ctx(qk, n, "c64", "fused", psi, ncb=3)
+    ctx.write_cbits(0, [1, 0, 1])
+    ref = oracle.OracleState(n, 3, psi=psi)
+    ref.cbits[:] = [1, 0, 1]
+    qk.run_ops(ctx, ops)
+    for op in ops:
+        oracle_apply(ref, op)
+    check_state(ctx.get_state(), ref.psi, "c64")
+    ctx.close()
+
+
+@pytest.mark.parametrize("n", [13, 16, 19])
+def test_fused_matches_plain_and_uses_few_passes(qk, n):
+    circ = workloads.layered_circuit(n, seed=9, n_gates=400)
+    got = {}
+    for mode in MODES:
+        ctx = qk.run_circuit(circ, "c64", mode)
+        ctx.sync()
+        got[mode] = (ctx.get_state(), ctx.counters())
+        ctx.close()
+    assert np.max(np.abs(got["fused"][0] - got["plain"][0])) < 1e-4
+    assert got["fused"][1]["launches"] < got["plain"][1]["launches"] / 10

@@ -251,25 +251,43 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return t;  // valid in thread 0
 }
 
+// prefix value of the decided outcomes: sum_j m_j << pos[j], j < k
+__device__ __forceinline__ uint64_t prefix_value(const MeasArgs &a, const MeasSlot *slots, int k) {
+    uint64_t v = 0;
+    for (int j = 0; j < k; ++j) v |= (uint64_t)(slots[j].m & 1) << a.pos[j];
+    return v;
+}
+
+__device__ __forceinline__ uint64_t insert_bits(uint64_t j, const MeasArgs &a) {
+    for (int t = 0; t < a.nins; ++t) {
+        const uint64_t lo = j & ((1ull << a.ins[t]) - 1);
+        j = ((j - lo) << 1) | lo;
+    }
+    return j;
+}
+
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_meas_reduce(const typename Amp<R>::T *__restrict__ psi, uint64_t n_amps,
-                                                          int q, double *partials) {
+__global__ void __launch_bounds__(kThreads) k_meas_reduce(const typename Amp<R>::T *__restrict__ psi, MeasArgs a,
+                                                          const MeasSlot *slots, double *partials) {
     __shared__ double sh[kThreads / 32];
+    const uint64_t pv = prefix_value(a, slots, a.k);
+    const int q = a.pos[a.k];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool bit0_free = a.nins == 0 || a.ins[0] != 0;
     double d0 = 0.0, d1 = 0.0;
-    if constexpr (sizeof(R) == 4) {
-        const float4 *p = reinterpret_cast<const float4 *>(psi);
-        const uint64_t n_units = n_amps >> 1;   // two amplitudes per float4
+    if (sizeof(R) == 4 && bit0_free && a.n_units >= 2) {
+        // two adjacent amplitudes (one 16-byte vector) per unit
+        const uint64_t n_units = a.n_units >> 1;
         for (uint64_t base = tid; base < n_units; base += 4 * stride) {
             float f0 = 0.f, f1 = 0.f;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const uint64_t u = base + (uint64_t)k * stride;
                 if (u < n_units) {
-                    const float4 v = p[u];
+                    const uint64_t i = insert_bits(u << 1, a) | pv;
+                    const float4 v = *reinterpret_cast<const float4 *>(psi + i);
                     const float pa = v.x * v.x + v.y * v.y, pb = v.z * v.z + v.w * v.w;
-                    const uint64_t i = u << 1;
                     if (q == 0) {
                         f0 += pa;
                         f1 += pb;
@@ -284,7 +302,8 @@ __global__ void __launch_bounds__(kThreads) k_meas_reduce(const typename Amp<R>:
             d1 += (double)f1;
         }
     } else {
-        for (uint64_t i = tid; i < n_amps; i += stride) {
+        for (uint64_t u = tid; u < a.n_units; u += stride) {
+            const uint64_t i = insert_bits(u, a) | pv;
             const typename Amp<R>::T v = psi[i];
             const double pa = (double)v.x * v.x + (double)v.y * v.y;
             if ((i >> q) & 1u) d1 += pa; else d0 += pa;
@@ -320,29 +339,41 @@ __global__ void __launch_bounds__(kThreads) k_meas_decide(const double *partials
     }
 }
 
+// Project onto the decided outcomes of every measured qubit and renormalise:
+// amplitudes that match keep a * 1/sqrt(P), the others are written as zero
+// without being read.
 template <typename R>
-__global__ void __launch_bounds__(kThreads) k_meas_collapse(typename Amp<R>::T *psi, uint64_t n_amps, int q,
-                                                            const MeasSlot *slot) {
-    const int m = slot->m;
-    const R sc = (R)slot->scale;
+__global__ void __launch_bounds__(kThreads) k_meas_collapse(typename Amp<R>::T *psi, uint64_t n_amps, MeasArgs a,
+                                                            const MeasSlot *slots) {
+    uint64_t M = 0;
+    for (int j = 0; j < a.k; ++j) M |= 1ull << a.pos[j];
+    const uint64_t V = prefix_value(a, slots, a.k);
+    const R sc = (R)slots[a.k - 1].scale;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if constexpr (sizeof(R) == 4) {
         float4 *p = reinterpret_cast<float4 *>(psi);
         for (uint64_t u = tid; u < (n_amps >> 1); u += stride) {
-            float4 v = p[u];
             const uint64_t i = u << 1;
-            const float ka = ((int)((i >> q) & 1u) == m) ? sc : 0.f;
-            const float kb = ((int)(((i + 1) >> q) & 1u) == m) ? sc : 0.f;
-            v.x *= ka; v.y *= ka; v.z *= kb; v.w *= kb;
+            const bool ka = (i & M) == V, kb = ((i + 1) & M) == V;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ka || kb) {
+                v = p[u];
+                const float sa = ka ? sc : 0.f, sb = kb ? sc : 0.f;
+                v.x *= sa; v.y *= sa; v.z *= sb; v.w *= sb;
+            }
             p[u] = v;
         }
     } else {
         for (uint64_t i = tid; i < n_amps; i += stride) {
-            typename Amp<R>::T v = psi[i];
-            const R k = ((int)((i >> q) & 1u) == m) ? sc : (R)0;
-            v.x *= k;
-            v.y *= k;
+            typename Amp<R>::T v;
+            v.x = 0;
+            v.y = 0;
+            if ((i & M) == V) {
+                v = psi[i];
+                v.x *= sc;
+                v.y *= sc;
+            }
             psi[i] = v;
         }
     }
@@ -438,14 +469,13 @@ cudaError_t launch_perm(int prec, const void *in, void *out, const PermArgs &a, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_measure_reduce(int prec, const void *psi, int n, int q, double *partials,
-                                  int nblocks, cudaStream_t s) {
-    const uint64_t n_amps = 1ull << n;
+cudaError_t launch_measure_reduce(int prec, const void *psi, int n, const MeasArgs &a, const MeasSlot *slots,
+                                  double *partials, int nblocks, cudaStream_t s) {
     if (n < 1) return cudaErrorInvalidValue;
     if (prec == 0)
-        k_meas_reduce<float><<<nblocks, kThreads, 0, s>>>((const float2 *)psi, n_amps, q, partials);
+        k_meas_reduce<float><<<nblocks, kThreads, 0, s>>>((const float2 *)psi, a, slots, partials);
     else
-        k_meas_reduce<double><<<nblocks, kThreads, 0, s>>>((const double2 *)psi, n_amps, q, partials);
+        k_meas_reduce<double><<<nblocks, kThreads, 0, s>>>((const double2 *)psi, a, slots, partials);
     return cudaGetLastError();
 }
 
@@ -455,13 +485,13 @@ cudaError_t launch_measure_decide(const double *partials, int nblocks, double u,
     return cudaGetLastError();
 }
 
-cudaError_t launch_measure_collapse(int prec, void *psi, int n, int q, const MeasSlot *slot, int sms,
+cudaError_t launch_measure_collapse(int prec, void *psi, int n, const MeasArgs &a, const MeasSlot *slots, int sms,
                                     cudaStream_t s) {
     const uint64_t n_amps = 1ull << n;
     if (prec == 0)
-        k_meas_collapse<float><<<grid_for(n_amps >> 1, sms), kThreads, 0, s>>>((float2 *)psi, n_amps, q, slot);
+        k_meas_collapse<float><<<grid_for(n_amps >> 1, sms), kThreads, 0, s>>>((float2 *)psi, n_amps, a, slots);
     else
-        k_meas_collapse<double><<<grid_for(n_amps, sms), kThreads, 0, s>>>((double2 *)psi, n_amps, q, slot);
+        k_meas_collapse<double><<<grid_for(n_amps, sms), kThreads, 0, s>>>((double2 *)psi, n_amps, a, slots);
     return cudaGetLastError();
 }
 

@@ -1,111 +1,210 @@
 // K3: fused tile pass for complex64 states.
 //
-// One CTA owns one tile of 2^13 amplitudes (13 physical qubits S[0..12], the
-// other n-13 bits fixed by the tile index).  The tile is read from HBM once,
+// One CTA owns one tile of 2^13 amplitudes (13 physical qubits S[0..12]; the
+// other n-13 bits are fixed by the tile index).  The tile is read from HBM once,
 // a program of gates runs on it, and it is written back once, so a pass costs
 // one read + one write of the state however many gates it carries.
 //
-// Amplitudes live in registers (32 per thread).  A 2x2 gate on a register bit
-// is a butterfly between two registers of the same thread; the register bits
-// are changed by transposing the tile through shared memory (three fixed
-// arrangements, see qk_kernels.cuh).  Diagonal gates are not applied one by one:
-// each thread keeps a factored diagonal -- a constant c0 and one factor a[k]
-// per register bit -- and multiplies it into the amplitudes only when a
-// non-commuting gate or a transpose needs it (a factor on the target bit of
-// a 2x2 gate is folded into that gate's matrix instead).
+// Each of the 256 threads holds 32 amplitudes in registers, split into real and
+// imaginary parts and packed two amplitudes per 64-bit register pair
+// (re[2j], re[2j+1]) / (im[2j], im[2j+1]), so that a 2x2 gate on register bit
+// k >= 1 runs on Blackwell's paired FP32 instructions (two lanes of math per
+// instruction).  The register bits are changed by transposing the tile through
+// shared memory (three fixed arrangements, see qk_kernels.cuh).
+//
+// Diagonal gates are not applied one by one: each thread keeps a pending
+// diagonal D(r) = exp(2 pi i (t0 + sum_{k in r} t_k) / 2^32) as six 32-bit
+// fixed-point phase sums (exact modulo one turn), and multiplies it into the
+// amplitudes only when a transpose or a gate that does not commute with it needs
+// that; a pending factor on the target bit of a 2x2 gate is folded into the
+// gate's matrix instead.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <utility>
 
 #include "qk_kernels.cuh"
 
 namespace qk {
 namespace {
 
+__host__ __device__ constexpr int ctz_const(int x) { return (x & 1) ? 0 : 1 + ctz_const(x >> 1); }
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 cmac2(float2 m0, float2 a, float2 m1, float2 b) {
-    float2 r;
-    r.x = m0.x * a.x - m0.y * a.y + m1.x * b.x - m1.y * b.y;
-    r.y = m0.x * a.y + m0.y * a.x + m1.x * b.y + m1.y * b.x;
-    return r;
+__device__ __forceinline__ float2 splat(float x) { return make_float2(x, x); }
+
+// exp(2 pi i t / 2^32)
+__device__ __forceinline__ float2 turns_to_phase(uint32_t t) {
+    const float x = (float)(int32_t)t * 0x1p-31f;  // in [-1, 1): angle = pi * x
+    float s, c;
+    sincospif(x, &s, &c);
+    return make_float2(c, s);
 }
 
-__host__ __device__ constexpr int ctz_const(int x) { return (x & 1) ? 0 : 1 + ctz_const(x >> 1); }
+// Amplitudes of one thread: R[j] = (re[2j], re[2j+1]), I[j] = (im[2j], im[2j+1]).
+struct Regs {
+    float2 R[16], I[16];
+};
 
-// Shared-memory slot of local index L: XOR-fold of the bits above 4 into the
-// low 4 bits.  Every arrangement's warp access then touches 16 distinct 8-byte
-// bank pairs per half warp (no conflicts).
-__device__ __forceinline__ int swz(int L) { return L ^ (((L >> 4) ^ (L >> 8) ^ (L >> 12)) & 15); }
+template <int r>
+__device__ __forceinline__ float &re_of(Regs &v) {
+    if constexpr (r & 1) return v.R[r >> 1].y;
+    else return v.R[r >> 1].x;
+}
+template <int r>
+__device__ __forceinline__ float &im_of(Regs &v) {
+    if constexpr (r & 1) return v.I[r >> 1].y;
+    else return v.I[r >> 1].x;
+}
+
+// Shared-memory slot (in floats, separate real and imaginary planes) of local
+// index L.  The map is linear over GF(2), so slot(thread part ^ register part)
+// = slot(thread part) ^ slot(register part), and every arrangement's warp access
+// touches 32 distinct banks.
+__host__ __device__ constexpr int slot4(int L) { return L ^ (((L >> 5) ^ (L >> 10)) & 31); }
 
 template <int ARR>
-__device__ __forceinline__ int local_index(int r, int lane, int warp) {
-    if constexpr (ARR == ARR_IO) return lane | (r << 5) | (warp << 10);
-    else if constexpr (ARR == ARR_LO) return r | (lane << 5) | (warp << 10);
-    else return lane | (r << 8) | (warp << 5);
+__host__ __device__ constexpr int reg_part(int r) {
+    return ARR == ARR_IO ? (r << 5) : ARR == ARR_LO ? r : (r << 8);
+}
+template <int ARR>
+__device__ __forceinline__ int thread_part(int lane, int warp) {
+    if constexpr (ARR == ARR_IO) return lane | (warp << 10);
+    else if constexpr (ARR == ARR_LO) return (lane << 5) | (warp << 10);
+    else return lane | (warp << 5);
+}
+
+template <int ARR, int r>
+__device__ __forceinline__ void put_one(float *sre, float *sim, Regs &v, int tslot) {
+    constexpr int rs = slot4(reg_part<ARR>(r));
+    sre[tslot ^ rs] = re_of<r>(v);
+    sim[tslot ^ rs] = im_of<r>(v);
+}
+template <int ARR, int r>
+__device__ __forceinline__ void get_one(const float *sre, const float *sim, Regs &v, int tslot) {
+    constexpr int rs = slot4(reg_part<ARR>(r));
+    re_of<r>(v) = sre[tslot ^ rs];
+    im_of<r>(v) = sim[tslot ^ rs];
+}
+
+template <int ARR, int... rs>
+__device__ __forceinline__ void put_all(float *sre, float *sim, Regs &v, int tslot, std::integer_sequence<int, rs...>) {
+    (put_one<ARR, rs>(sre, sim, v, tslot), ...);
+}
+template <int ARR, int... rs>
+__device__ __forceinline__ void get_all(const float *sre, const float *sim, Regs &v, int tslot,
+                                        std::integer_sequence<int, rs...>) {
+    (get_one<ARR, rs>(sre, sim, v, tslot), ...);
 }
 
 template <int ARR>
-__device__ __forceinline__ void to_smem(float2 *sm, const float2 (&v)[32], int lane, int warp) {
-#pragma unroll
-    for (int r = 0; r < 32; ++r) sm[swz(local_index<ARR>(r, lane, warp))] = v[r];
+__device__ __forceinline__ void to_smem(float *sre, float *sim, Regs &v, int lane, int warp) {
+    put_all<ARR>(sre, sim, v, slot4(thread_part<ARR>(lane, warp)), std::make_integer_sequence<int, 32>{});
 }
-
 template <int ARR>
-__device__ __forceinline__ void from_smem(const float2 *sm, float2 (&v)[32], int lane, int warp) {
-#pragma unroll
-    for (int r = 0; r < 32; ++r) v[r] = sm[swz(local_index<ARR>(r, lane, warp))];
+__device__ __forceinline__ void from_smem(const float *sre, const float *sim, Regs &v, int lane, int warp) {
+    get_all<ARR>(sre, sim, v, slot4(thread_part<ARR>(lane, warp)), std::make_integer_sequence<int, 32>{});
 }
 
-__device__ __forceinline__ void transpose(float2 (&v)[32], float2 *sm, int from, int to, int lane, int warp) {
+__device__ __forceinline__ void transpose(Regs &v, float *sre, float *sim, int from, int to, int lane, int warp) {
     __syncthreads();
-    if (from == ARR_IO) to_smem<ARR_IO>(sm, v, lane, warp);
-    else if (from == ARR_LO) to_smem<ARR_LO>(sm, v, lane, warp);
-    else to_smem<ARR_HI>(sm, v, lane, warp);
+    if (from == ARR_IO) to_smem<ARR_IO>(sre, sim, v, lane, warp);
+    else if (from == ARR_LO) to_smem<ARR_LO>(sre, sim, v, lane, warp);
+    else to_smem<ARR_HI>(sre, sim, v, lane, warp);
     __syncthreads();
-    if (to == ARR_IO) from_smem<ARR_IO>(sm, v, lane, warp);
-    else if (to == ARR_LO) from_smem<ARR_LO>(sm, v, lane, warp);
-    else from_smem<ARR_HI>(sm, v, lane, warp);
+    if (to == ARR_IO) from_smem<ARR_IO>(sre, sim, v, lane, warp);
+    else if (to == ARR_LO) from_smem<ARR_LO>(sre, sim, v, lane, warp);
+    else from_smem<ARR_HI>(sre, sim, v, lane, warp);
 }
 
-// 2x2 butterfly on register bit K; with CTRL only for pairs whose register
-// index has every bit of rmask set.
-template <int K, bool CTRL>
-__device__ __forceinline__ void u2_reg(float2 (&v)[32], float2 m00, float2 m01, float2 m10, float2 m11, int rmask) {
+struct Mat {
+    float2 a00r, a00i, n00i, a01r, a01i, n01i, a10r, a10i, n10i, a11r, a11i, n11i;
+    __device__ __forceinline__ Mat(float2 m00, float2 m01, float2 m10, float2 m11) {
+        a00r = splat(m00.x); a00i = splat(m00.y); n00i = splat(-m00.y);
+        a01r = splat(m01.x); a01i = splat(m01.y); n01i = splat(-m01.y);
+        a10r = splat(m10.x); a10i = splat(m10.y); n10i = splat(-m10.y);
+        a11r = splat(m11.x); a11i = splat(m11.y); n11i = splat(-m11.y);
+    }
+};
+
+// 2x2 gate on register bit K >= 1: couples (j, j | 2^(K-1)) of packed registers,
+// two amplitude pairs per instruction.  A couple acts if (2j & rmask) == rmask;
+// with register bit 0 in rmask only the odd halves act (the even halves keep
+// their old values).
+template <int K>
+__device__ __forceinline__ void u2_packed(Regs &v, const Mat &M, int rmask) {
+    static_assert(K >= 1 && K <= 4, "packed butterflies need K >= 1");
+    const bool odd_only = rmask & 1;
+    const int hmask = rmask & ~1;
 #pragma unroll
-    for (int p = 0; p < 16; ++p) {
-        const int r0 = ((p >> K) << (K + 1)) | (p & ((1 << K) - 1));
-        const int r1 = r0 | (1 << K);
-        if (!CTRL || (r0 & rmask) == rmask) {
-            const float2 a = v[r0], b = v[r1];
-            v[r0] = cmac2(m00, a, m01, b);
-            v[r1] = cmac2(m10, a, m11, b);
+    for (int j = 0; j < 16; ++j) {
+        if (j & (1 << (K - 1))) continue;
+        const int j1 = j | (1 << (K - 1));
+        if (((j << 1) & hmask) != hmask) continue;
+        const float2 A = v.R[j], B = v.I[j], C = v.R[j1], D = v.I[j1];
+        float2 r0 = __fmul2_rn(M.a00r, A);
+        r0 = __ffma2_rn(M.n00i, B, r0);
+        r0 = __ffma2_rn(M.a01r, C, r0);
+        r0 = __ffma2_rn(M.n01i, D, r0);
+        float2 i0 = __fmul2_rn(M.a00r, B);
+        i0 = __ffma2_rn(M.a00i, A, i0);
+        i0 = __ffma2_rn(M.a01r, D, i0);
+        i0 = __ffma2_rn(M.a01i, C, i0);
+        float2 r1 = __fmul2_rn(M.a10r, A);
+        r1 = __ffma2_rn(M.n10i, B, r1);
+        r1 = __ffma2_rn(M.a11r, C, r1);
+        r1 = __ffma2_rn(M.n11i, D, r1);
+        float2 i1 = __fmul2_rn(M.a10r, B);
+        i1 = __ffma2_rn(M.a10i, A, i1);
+        i1 = __ffma2_rn(M.a11r, D, i1);
+        i1 = __ffma2_rn(M.a11i, C, i1);
+        if (odd_only) {
+            r0.x = A.x; i0.x = B.x; r1.x = C.x; i1.x = D.x;
+        }
+        v.R[j] = r0; v.I[j] = i0; v.R[j1] = r1; v.I[j1] = i1;
+    }
+}
+
+// 2x2 gate on register bit 0: the pair is the two halves of one packed register.
+__device__ __forceinline__ void u2_bit0(Regs &v, float2 m00, float2 m01, float2 m10, float2 m11, int rmask) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (((j << 1) & rmask) != rmask) continue;
+        const float2 a = make_float2(v.R[j].x, v.I[j].x), b = make_float2(v.R[j].y, v.I[j].y);
+        const float2 o0 = make_float2(m00.x * a.x - m00.y * a.y + m01.x * b.x - m01.y * b.y,
+                                      m00.x * a.y + m00.y * a.x + m01.x * b.y + m01.y * b.x);
+        const float2 o1 = make_float2(m10.x * a.x - m10.y * a.y + m11.x * b.x - m11.y * b.y,
+                                      m10.x * a.y + m10.y * a.x + m11.x * b.y + m11.y * b.x);
+        v.R[j] = make_float2(o0.x, o1.x);
+        v.I[j] = make_float2(o0.y, o1.y);
+    }
+}
+
+// amplitudes with register bit K set are multiplied by f
+template <int K>
+__device__ __forceinline__ void bit_factor(Regs &v, float2 f) {
+    if constexpr (K == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float xr = v.R[j].y, xi = v.I[j].y;
+            v.R[j].y = xr * f.x - xi * f.y;
+            v.I[j].y = xr * f.y + xi * f.x;
+        }
+    } else {
+        const float2 fr = splat(f.x), fi = splat(f.y), nfi = splat(-f.y);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (!(j & (1 << (K - 1)))) continue;
+            const float2 A = v.R[j], B = v.I[j];
+            v.R[j] = __ffma2_rn(nfi, B, __fmul2_rn(fr, A));
+            v.I[j] = __ffma2_rn(fi, A, __fmul2_rn(fr, B));
         }
     }
 }
 
-template <bool CTRL>
-__device__ __forceinline__ void u2_dispatch(int k, float2 (&v)[32], float2 m00, float2 m01, float2 m10, float2 m11,
-                                            int rmask) {
-    switch (k) {
-        case 0: u2_reg<0, CTRL>(v, m00, m01, m10, m11, rmask); break;
-        case 1: u2_reg<1, CTRL>(v, m00, m01, m10, m11, rmask); break;
-        case 2: u2_reg<2, CTRL>(v, m00, m01, m10, m11, rmask); break;
-        case 3: u2_reg<3, CTRL>(v, m00, m01, m10, m11, rmask); break;
-        default: u2_reg<4, CTRL>(v, m00, m01, m10, m11, rmask); break;
-    }
-}
-
-// v[r] *= f for every r with register bit K set
-template <int K>
-__device__ __forceinline__ void bit_factor(float2 (&v)[32], float2 f) {
-#pragma unroll
-    for (int r = 0; r < 32; ++r)
-        if (r & (1 << K)) v[r] = cmul(v[r], f);
-}
-
-__device__ __forceinline__ void bit_factor_dispatch(int k, float2 (&v)[32], float2 f) {
+__device__ __forceinline__ void bit_factor_dispatch(int k, Regs &v, float2 f) {
     switch (k) {
         case 0: bit_factor<0>(v, f); break;
         case 1: bit_factor<1>(v, f); break;
@@ -115,64 +214,73 @@ __device__ __forceinline__ void bit_factor_dispatch(int k, float2 (&v)[32], floa
     }
 }
 
-// Pending factored diagonal of one thread: D(r) = c0 * prod_{k in r} a[k].
+// Pending diagonal of one thread in 32-bit fixed-point turns.
 struct Pending {
-    float2 c0;
-    float2 a[5];
-    int mask;  // bit k: a[k] != 1; bit 5: c0 != 1
+    uint32_t t0, t[5];
+    int mask;  // bit k: t[k] may be nonzero; bit 5: t0 may be nonzero
 
     __device__ __forceinline__ void reset() {
-        c0 = make_float2(1.f, 0.f);
+        t0 = 0;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) a[k] = make_float2(1.f, 0.f);
+        for (int k = 0; k < 5; ++k) t[k] = 0;
         mask = 0;
     }
-    __device__ __forceinline__ float2 get(int k) const {
+    __device__ __forceinline__ uint32_t get(int k) const {
         switch (k) {
-            case 0: return a[0];
-            case 1: return a[1];
-            case 2: return a[2];
-            case 3: return a[3];
-            default: return a[4];
+            case 0: return t[0];
+            case 1: return t[1];
+            case 2: return t[2];
+            case 3: return t[3];
+            default: return t[4];
         }
     }
-    __device__ __forceinline__ void mul(int k, float2 f) {
+    __device__ __forceinline__ void add(int k, uint32_t d) {
         switch (k) {
-            case 0: a[0] = cmul(a[0], f); break;
-            case 1: a[1] = cmul(a[1], f); break;
-            case 2: a[2] = cmul(a[2], f); break;
-            case 3: a[3] = cmul(a[3], f); break;
-            default: a[4] = cmul(a[4], f); break;
+            case 0: t[0] += d; break;
+            case 1: t[1] += d; break;
+            case 2: t[2] += d; break;
+            case 3: t[3] += d; break;
+            default: t[4] += d; break;
         }
         mask |= 1 << k;
     }
     __device__ __forceinline__ void clear(int k) {
         switch (k) {
-            case 0: a[0] = make_float2(1.f, 0.f); break;
-            case 1: a[1] = make_float2(1.f, 0.f); break;
-            case 2: a[2] = make_float2(1.f, 0.f); break;
-            case 3: a[3] = make_float2(1.f, 0.f); break;
-            default: a[4] = make_float2(1.f, 0.f); break;
+            case 0: t[0] = 0; break;
+            case 1: t[1] = 0; break;
+            case 2: t[2] = 0; break;
+            case 3: t[3] = 0; break;
+            default: t[4] = 0; break;
         }
         mask &= ~(1 << k);
     }
-    // multiply the whole pending diagonal into the registers
-    __device__ __forceinline__ void flush(float2 (&v)[32]) {
+    __device__ __forceinline__ void flush(Regs &v) {
         if (mask == 0) return;
         if ((mask & 32) == 0 && __popc(mask) <= 2) {
 #pragma unroll
             for (int k = 0; k < 5; ++k)
-                if (mask & (1 << k)) bit_factor_dispatch(k, v, a[k]);
+                if ((mask & (1 << k)) && t[k] != 0) bit_factor_dispatch(k, v, turns_to_phase(t[k]));
         } else {
-            // walk r in Gray-code order so that D(r) changes by one factor per step
-            float2 d = c0;
-            v[0] = cmul(v[0], d);
+            // D(r) = c0 * prod_{k in r} a_k: six sincos, then walk j (register
+            // bits 1..4) in Gray-code order so D changes by one factor per step
+            const float2 c0 = (mask & 32) ? turns_to_phase(t0) : make_float2(1.f, 0.f);
+            float2 a[5];
 #pragma unroll
-            for (int i = 1; i < 32; ++i) {
-                const int g = i ^ (i >> 1), gp = (i - 1) ^ ((i - 1) >> 1);
-                const int b = ctz_const(g ^ gp);
-                d = cmul(d, (g & (1 << b)) ? a[b] : conjf2(a[b]));
-                v[g] = cmul(v[g], d);
+            for (int k = 0; k < 5; ++k) a[k] = (mask & (1 << k)) ? turns_to_phase(t[k]) : make_float2(1.f, 0.f);
+            float2 d = c0;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int g = i ^ (i >> 1);
+                if (i > 0) {
+                    const int gp = (i - 1) ^ ((i - 1) >> 1);
+                    const int b = ctz_const(g ^ gp);         // register bit b + 1 toggles
+                    d = cmul(d, (g >> b) & 1 ? a[b + 1] : make_float2(a[b + 1].x, -a[b + 1].y));
+                }
+                const float2 d1 = cmul(d, a[0]);
+                const float2 Dr = make_float2(d.x, d1.x), Di = make_float2(d.y, d1.y);
+                const float2 A = v.R[g], B = v.I[g];
+                v.R[g] = __ffma2_rn(make_float2(-Di.x, -Di.y), B, __fmul2_rn(Dr, A));
+                v.I[g] = __ffma2_rn(Di, A, __fmul2_rn(Dr, B));
             }
         }
         reset();
@@ -186,9 +294,39 @@ __device__ __forceinline__ bool op_applies(const TileOp &op, int tbits, uint64_t
     return true;
 }
 
+// global element offsets of the 32 registers: bits of r select strides
+template <typename Off>
+struct Offsets {
+    Off o01[4], o23[4], s4;
+    __device__ __forceinline__ void init(Off s0, Off s1, Off s2, Off s3, Off s4_) {
+        o01[0] = 0; o01[1] = s0; o01[2] = s1; o01[3] = s0 + s1;
+        o23[0] = 0; o23[1] = s2; o23[2] = s3; o23[3] = s2 + s3;
+        s4 = s4_;
+    }
+    template <int r>
+    __device__ __forceinline__ Off at() const {
+        return o01[r & 3] + o23[(r >> 2) & 3] + ((r & 16) ? s4 : (Off)0);
+    }
+};
+
+template <typename Off, int... rs>
+__device__ __forceinline__ void load_all(const float2 *src, const Offsets<Off> &o, Regs &v,
+                                         std::integer_sequence<int, rs...>) {
+    float2 tmp[32];
+    ((tmp[rs] = __ldcs(src + o.template at<rs>())), ...);
+    ((re_of<rs>(v) = tmp[rs].x, im_of<rs>(v) = tmp[rs].y), ...);
+}
+template <typename Off, int... rs>
+__device__ __forceinline__ void store_all(float2 *dst, const Offsets<Off> &o, Regs &v,
+                                          std::integer_sequence<int, rs...>) {
+    (__stcs(dst + o.template at<rs>(), make_float2(re_of<rs>(v), im_of<rs>(v))), ...);
+}
+
+template <typename Off>
 __global__ void __launch_bounds__(kTileThreads, 2)
     k_tile(float2 *__restrict__ psi, const __grid_constant__ TileParams P, const uint8_t *__restrict__ cbits) {
-    extern __shared__ __align__(16) float2 sm[];   // 2^13 amplitudes (64 KiB)
+    extern __shared__ __align__(16) float smf[];   // 2 x 2^13 floats (64 KiB)
+    float *sre = smf, *sim = smf + (1 << kTileQubits);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tbits = (warp << 5) | lane;
 
@@ -204,21 +342,15 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         for (int b = 0; b < P.nfix; ++b) base |= ((tile >> b) & 1ull) << P.fixed[b];
 
         // load in ARR_IO: lanes = local 0..4, registers = local 5..9, warps = local 10..12
-        float2 v[32];
+        Regs v;
         {
             uint64_t tb = base + (uint64_t)lane;
 #pragma unroll
             for (int j = 0; j < 3; ++j)
                 if ((warp >> j) & 1) tb += 1ull << P.S[10 + j];
-            const float2 *src = psi + tb;
-#pragma unroll
-            for (int r = 0; r < 32; ++r) {
-                uint64_t off = 0;
-#pragma unroll
-                for (int k = 0; k < 5; ++k)
-                    if ((r >> k) & 1) off += 1ull << P.S[5 + k];
-                v[r] = src[off];
-            }
+            Offsets<Off> o;
+            o.init((Off)1 << P.S[5], (Off)1 << P.S[6], (Off)1 << P.S[7], (Off)1 << P.S[8], (Off)1 << P.S[9]);
+            load_all<Off>(psi + tb, o, v, std::make_integer_sequence<int, 32>{});
         }
 
         Pending pd;
@@ -228,7 +360,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
             const TileOp &op = P.ops[i];
             if (op.kind == TOP_XPOSE) {
                 pd.flush(v);
-                transpose(v, sm, cur, op.k, lane, warp);
+                transpose(v, sre, sim, cur, op.k, lane, warp);
                 cur = op.k;
                 continue;
             }
@@ -238,38 +370,60 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                 float2 m10 = make_float2(op.m[4], op.m[5]), m11 = make_float2(op.m[6], op.m[7]);
                 const int k = op.k;
                 if (pd.mask & (1 << k)) {
-                    const float2 ak = pd.get(k);
-                    if (op.rmask == 0) {  // fold diag(1, a_k) into the gate: U * diag(1, a_k)
-                        m01 = cmul(m01, ak);
-                        m11 = cmul(m11, ak);
-                    } else {
-                        bit_factor_dispatch(k, v, ak);
+                    const uint32_t tk = pd.get(k);
+                    if (tk != 0) {
+                        const float2 ak = turns_to_phase(tk);
+                        if (op.rmask == 0) {  // fold diag(1, a_k) into the gate: U * diag(1, a_k)
+                            m01 = cmul(m01, ak);
+                            m11 = cmul(m11, ak);
+                        } else {
+                            bit_factor_dispatch(k, v, ak);
+                        }
                     }
                     pd.clear(k);
                 }
-                if (op.rmask) u2_dispatch<true>(k, v, m00, m01, m10, m11, op.rmask);
-                else u2_dispatch<false>(k, v, m00, m01, m10, m11, 0);
-            } else {  // TOP_PHASE: factor f where (register index & rmask) == rval
-                const float2 f = make_float2(op.m[0], op.m[1]);
+                if (k == 0) {
+                    u2_bit0(v, m00, m01, m10, m11, op.rmask);
+                } else {
+                    const Mat M(m00, m01, m10, m11);
+                    switch (k) {
+                        case 1: u2_packed<1>(v, M, op.rmask); break;
+                        case 2: u2_packed<2>(v, M, op.rmask); break;
+                        case 3: u2_packed<3>(v, M, op.rmask); break;
+                        default: u2_packed<4>(v, M, op.rmask); break;
+                    }
+                }
+            } else {  // TOP_PHASE: factor where (register index & rmask) == rval
                 const int rm = op.rmask;
                 const int pc = __popc(rm);
                 if (pc == 0) {
-                    pd.c0 = cmul(pd.c0, f);
+                    pd.t0 += op.ph.turns;
                     pd.mask |= 32;
                 } else if (pc == 1) {
                     const int k = __ffs(rm) - 1;
                     if (op.rval) {
-                        pd.mul(k, f);
+                        pd.add(k, op.ph.turns);
                     } else {  // f on bit k = 0:  f * (f^-1 on bit k = 1)
-                        pd.c0 = cmul(pd.c0, f);
+                        pd.t0 += op.ph.turns;
                         pd.mask |= 32;
-                        pd.mul(k, conjf2(f));
+                        pd.add(k, 0u - op.ph.turns);
                     }
                 } else {
                     const int rv = op.rval;
+                    const float2 f = make_float2(op.ph.re, op.ph.im);
 #pragma unroll
-                    for (int r = 0; r < 32; ++r)
-                        if ((r & rm) == rv) v[r] = cmul(v[r], f);
+                    for (int j = 0; j < 16; ++j) {
+                        if (((2 * j) & rm) == rv) {
+                            const float xr = v.R[j].x, xi = v.I[j].x;
+                            v.R[j].x = xr * f.x - xi * f.y;
+                            v.I[j].x = xr * f.y + xi * f.x;
+                        }
+                        if (((2 * j + 1) & rm) == rv) {
+                            const float xr = v.R[j].y, xi = v.I[j].y;
+                            v.R[j].y = xr * f.x - xi * f.y;
+                            v.I[j].y = xr * f.y + xi * f.x;
+                        }
+                    }
                 }
             }
         }
@@ -278,52 +432,45 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         // store in ARR_IO or ARR_HI (lanes = local 0..4 in both)
         {
             uint64_t tb = base + (uint64_t)lane;
+            Offsets<Off> o;
             if (cur == ARR_IO) {
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
                     if ((warp >> j) & 1) tb += 1ull << P.S[10 + j];
-                float2 *dst = psi + tb;
-#pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    uint64_t off = 0;
-#pragma unroll
-                    for (int k = 0; k < 5; ++k)
-                        if ((r >> k) & 1) off += 1ull << P.S[5 + k];
-                    dst[off] = v[r];
-                }
+                o.init((Off)1 << P.S[5], (Off)1 << P.S[6], (Off)1 << P.S[7], (Off)1 << P.S[8], (Off)1 << P.S[9]);
             } else {
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
                     if ((warp >> j) & 1) tb += 1ull << P.S[5 + j];
-                float2 *dst = psi + tb;
-#pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    uint64_t off = 0;
-#pragma unroll
-                    for (int k = 0; k < 5; ++k)
-                        if ((r >> k) & 1) off += 1ull << P.S[8 + k];
-                    dst[off] = v[r];
-                }
+                o.init((Off)1 << P.S[8], (Off)1 << P.S[9], (Off)1 << P.S[10], (Off)1 << P.S[11], (Off)1 << P.S[12]);
             }
+            store_all<Off>(psi + tb, o, v, std::make_integer_sequence<int, 32>{});
         }
         __syncthreads();  // shared memory is reused by the next tile's transposes
     }
 }
 
-}  // namespace
-
-cudaError_t launch_tile(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s) {
-    constexpr int smem = (int)sizeof(float2) << kTileQubits;
-    static bool attr_set = false;  // per process; the attribute is per function
+template <typename Off>
+cudaError_t launch_tile_t(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s) {
+    constexpr int smem = (int)(2 * sizeof(float)) << kTileQubits;
+    static bool attr_set = false;  // the attribute is per function, once per process
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_tile<Off>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     uint64_t grid = p.n_tiles;
     if (grid > (1ull << 30)) grid = 1ull << 30;
-    k_tile<<<(unsigned)grid, kTileThreads, smem, s>>>((float2 *)psi, p, cbits);
+    k_tile<Off><<<(unsigned)grid, kTileThreads, smem, s>>>((float2 *)psi, p, cbits);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tile(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s) {
+    // 32-bit element offsets inside a tile reach 2^32 amplitudes
+    if (p.n <= 32) return launch_tile_t<uint32_t>(psi, p, cbits, s);
+    return launch_tile_t<uint64_t>(psi, p, cbits, s);
 }
 
 }  // namespace qk

@@ -772,22 +772,32 @@ qk_status qk_measure(qk_ctx *c, const int *qubits, int nq, const double *uniform
     if (s != QK_OK) return s;
     s = ensure_slots(c, nq);
     if (s != QK_OK) return s;
-    const double fp = (double)full_pass_bytes(c);
-    for (int a = 0; a < nq; ++a) {
-        const int q = c->l2p[qubits[a]];
+    // decision k sums over the amplitudes that match decisions 0..k-1 (no
+    // collapse in between); one collapse pass projects onto all outcomes at the end
+    qk::MeasArgs ma{};
+    for (int a = 0; a < nq; ++a) ma.pos[a] = c->l2p[qubits[a]];
+    for (int k = 0; k < nq; ++k) {
+        ma.k = k;
+        ma.nins = k;
+        std::vector<int> ins(ma.pos, ma.pos + k);
+        std::sort(ins.begin(), ins.end());
+        for (int t = 0; t < k; ++t) ma.ins[t] = ins[t];
+        ma.n_units = 1ull << (c->n - k);
         {
-            LaunchScope ls(c, 5, fp / 2);
-            CUDA_TRY(c, qk::launch_measure_reduce((int)c->prec, c->d_state, c->n, q, c->d_partials, c->meas_blocks, c->stream));
+            LaunchScope ls(c, 5, (double)c->amp * (double)ma.n_units);
+            CUDA_TRY(c, qk::launch_measure_reduce((int)c->prec, c->d_state, c->n, ma, c->d_slots, c->d_partials,
+                                                  c->meas_blocks, c->stream));
         }
         {
             LaunchScope ls(c, 6, 0);
-            CUDA_TRY(c, qk::launch_measure_decide(c->d_partials, c->meas_blocks, uniforms[a], c->d_slots + a, c->d_cbits,
-                                                  dest ? dest[a] : -1, c->stream));
+            CUDA_TRY(c, qk::launch_measure_decide(c->d_partials, c->meas_blocks, uniforms[k], c->d_slots + k, c->d_cbits,
+                                                  dest ? dest[k] : -1, c->stream));
         }
-        {
-            LaunchScope ls(c, 5, fp);
-            CUDA_TRY(c, qk::launch_measure_collapse((int)c->prec, c->d_state, c->n, q, c->d_slots + a, c->sms, c->stream));
-        }
+    }
+    ma.k = nq;
+    {
+        LaunchScope ls(c, 5, (double)c->amp * (double)((1ull << c->n) + (1ull << (c->n - nq))));
+        CUDA_TRY(c, qk::launch_measure_collapse((int)c->prec, c->d_state, c->n, ma, c->d_slots, c->sms, c->stream));
     }
     if (outcome) {
         std::vector<qk::MeasSlot> h(nq);

@@ -79,6 +79,18 @@ struct MeasSlot {
     int pad;
 };
 
+// Measurement of a list of qubits, one decision at a time.  Decision k sums
+// |a_i|^2 over the indices whose earlier measured bits equal the outcomes
+// already decided (read from the slots on the device), split by bit pos[k].
+constexpr int kMaxMeasure = 64;
+struct MeasArgs {
+    int k;                // decisions already taken (prefix length); collapse: all decisions
+    int pos[40];          // physical bit of measured qubit j (list order), j < k and j == k
+    int nins;             // prefix bits sorted ascending, for enumeration
+    int ins[40];
+    uint64_t n_units;     // 2^(n-k) amplitudes match the prefix
+};
+
 // Qubit-relabelling gather: out[logical index] = in[physical index].
 struct RelabelArgs {
     int n;
@@ -113,7 +125,13 @@ struct TileOp {
     uint16_t cond;         // index into TileParams::conds, 0xffff = unconditional
     uint16_t pad;
     uint64_t gmask, gval;  // condition on the tile's fixed (non-tile) physical bits
-    float m[8];            // U2: m00, m01, m10, m11 as (re, im); PHASE: factor (re, im)
+    union {
+        float m[8];        // U2: m00, m01, m10, m11 as (re, im)
+        struct {
+            float re, im;  // PHASE: factor f = exp(2 pi i turns / 2^32)
+            uint32_t turns;
+        } ph;
+    };
 };
 
 struct TileParams {
@@ -142,11 +160,11 @@ cudaError_t launch_matk(int prec, void *psi, const MatKArgs &a, const uint8_t *c
                         cudaStream_t s);
 cudaError_t launch_perm(int prec, const void *in, void *out, const PermArgs &a, const uint8_t *cbits,
                         int sms, cudaStream_t s);
-cudaError_t launch_measure_reduce(int prec, const void *psi, int n, int q, double *partials,
-                                  int nblocks, cudaStream_t s);
+cudaError_t launch_measure_reduce(int prec, const void *psi, int n, const MeasArgs &a, const MeasSlot *slots,
+                                  double *partials, int nblocks, cudaStream_t s);
 cudaError_t launch_measure_decide(const double *partials, int nblocks, double u, MeasSlot *slot,
                                   uint8_t *cbits, int dest, cudaStream_t s);
-cudaError_t launch_measure_collapse(int prec, void *psi, int n, int q, const MeasSlot *slot, int sms,
+cudaError_t launch_measure_collapse(int prec, void *psi, int n, const MeasArgs &a, const MeasSlot *slots, int sms,
                                     cudaStream_t s);
 cudaError_t launch_set_basis(int prec, void *psi, uint64_t index, cudaStream_t s);
 cudaError_t launch_relabel(int prec, const void *in, void *out, const RelabelArgs &a, int sms,

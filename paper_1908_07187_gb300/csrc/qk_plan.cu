@@ -11,6 +11,7 @@
 // gates are list-scheduled over the three register arrangements of the tile
 // kernel, inserting a transpose when no ready gate fits the current one.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -228,8 +229,12 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             } else {
                 t.kind = TOP_PHASE;
                 encode_cond(op.mask, op.val, arr, local_of, t);
-                t.m[0] = (float)op.f.real();
-                t.m[1] = (float)op.f.imag();
+                t.ph.re = (float)op.f.real();
+                t.ph.im = (float)op.f.imag();
+                // the factor's angle as a fraction of a turn in 32-bit fixed point
+                double frac = std::arg(op.f) / (2.0 * M_PI);
+                if (frac < 0) frac += 1.0;
+                t.ph.turns = (uint32_t)(uint64_t)std::llround(frac * 4294967296.0);
             }
             done[j] = 1;
             ++ndone;

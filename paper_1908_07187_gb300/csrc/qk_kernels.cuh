@@ -112,10 +112,20 @@ struct RelabelArgs {
 // ---------------------------------------------------------------------------
 constexpr int kTileQubits = 13;
 constexpr int kTileThreads = 256;
-constexpr int kTileMaxOps = 400;
+constexpr int kTileMaxOps = 256;
+constexpr int kTileMaxEntries = 640;
 constexpr int kTileMaxConds = 4;
 enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
-enum TileOpKind : uint8_t { TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2 };
+// TOP_PHASES: a group of diagonal terms that all add to one pending phase sum
+// (register bit k, or the constant when k == 5); each entry adds its turns when
+// its thread-bit and fixed-bit conditions hold.
+enum TileOpKind : uint8_t { TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_PHASES = 3 };
+
+struct PhaseEntry {
+    uint16_t tmask, tval;
+    uint32_t turns;
+    uint64_t gmask, gval;
+};
 
 struct TileOp {
     uint8_t kind;          // TileOpKind
@@ -123,6 +133,8 @@ struct TileOp {
     uint8_t rmask, rval;   // condition on register bits (5-bit register index space)
     uint16_t tmask, tval;  // condition on thread bits: bits 0..4 lane, 5..7 warp
     uint16_t cond;         // index into TileParams::conds, 0xffff = unconditional
+    uint16_t count;        // TOP_PHASES: entries [first, first + count)
+    uint16_t first;
     uint16_t pad;
     uint64_t gmask, gval;  // condition on the tile's fixed (non-tile) physical bits
     union {
@@ -144,8 +156,11 @@ struct TileParams {
     int n_conds;
     Cond conds[kTileMaxConds];
     int nops;
+    int nentries;
     TileOp ops[kTileMaxOps];
+    PhaseEntry entries[kTileMaxEntries];
 };
+static_assert(sizeof(TileParams) <= 32764, "tile program must fit in the kernel parameter space");
 
 cudaError_t launch_tile(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s);
 

@@ -129,7 +129,9 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
     rem.reserve(ops.size());
     for (const auto &op : ops) rem.push_back(classify(op));
 
-    const int max_take = kTileMaxOps / 2 - 1;  // plus one transpose per gate at most, plus the last
+    // take limits per pass; halved and retried when a program overflows the
+    // kernel-parameter budget (ops and grouped phase entries)
+    int max_u2 = 100, max_ph = 300;
     std::vector<POp> left, taken;
     while (!rem.empty()) {
         // ---- choose S and the gates this pass takes
@@ -139,8 +141,10 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
         std::vector<Cond> conds;
         left.clear();
         taken.clear();
+        int n_u2 = 0, n_ph = 0;
         for (const POp &p : rem) {
-            bool ok = (int)taken.size() < max_take && !(p.nd & allb) && !(p.all & ndb);
+            const bool is_u2 = p.op->kind == FusedOp::U2;
+            bool ok = (is_u2 ? n_u2 < max_u2 : n_ph < max_ph) && !(p.nd & allb) && !(p.all & ndb);
             if (ok && p.op->kind == FusedOp::U2) {
                 const uint64_t t = 1ull << p.op->q;
                 if (!(S & t)) {
@@ -162,6 +166,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             }
             if (ok) {
                 taken.push_back(p);
+                if (is_u2) ++n_u2; else ++n_ph;
             } else {
                 left.push_back(p);
                 ndb |= p.nd;
@@ -208,9 +213,11 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 }
         std::vector<char> done(m, 0);
         int ndone = 0, cur = ARR_IO, nops = 0;
+        static thread_local std::vector<TileOp> prog;
+        prog.assign(2 * (size_t)m + 2, TileOp{});
         auto emit = [&](int j, int arr) {
             const FusedOp &op = *taken[j].op;
-            TileOp &t = P.ops[nops++];
+            TileOp &t = prog[nops++];
             std::memset(&t, 0, sizeof t);
             t.cond = 0xffff;
             if (op.cond.n)
@@ -260,7 +267,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                         best = a;
                     }
                 }
-                TileOp &t = P.ops[nops++];
+                TileOp &t = prog[nops++];
                 std::memset(&t, 0, sizeof t);
                 t.kind = TOP_XPOSE;
                 t.k = (uint8_t)best;
@@ -269,12 +276,87 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             }
         }
         if (cur == ARR_LO) {
-            TileOp &t = P.ops[nops++];
+            TileOp &t = prog[nops++];
             std::memset(&t, 0, sizeof t);
             t.kind = TOP_XPOSE;
             t.k = ARR_IO;
             t.cond = 0xffff;
             cur = ARR_IO;
+        }
+        // group runs of consecutive diagonal terms by the pending sum they feed
+        {
+            static thread_local TileOp out[2 * kTileMaxOps + 8];
+            int nout = 0, nent = 0;
+            bool overflow = false;
+            for (int i = 0; i < nops && !overflow;) {
+                if (nout >= 2 * kTileMaxOps) {
+                    overflow = true;
+                    break;
+                }
+                if (prog[i].kind != TOP_PHASE) {
+                    out[nout++] = prog[i++];
+                    continue;
+                }
+                int j = i;
+                while (j < nops && prog[j].kind == TOP_PHASE) ++j;
+                std::vector<PhaseEntry> grp[6];
+                for (int t = i; t < j; ++t) {
+                    const TileOp &o = prog[t];
+                    if (nout >= 2 * kTileMaxOps) {
+                        overflow = true;
+                        break;
+                    }
+                    const int pc = __builtin_popcount(o.rmask);
+                    if (o.cond != 0xffff || pc >= 2) {
+                        out[nout++] = o;   // applied directly
+                        continue;
+                    }
+                    PhaseEntry e;
+                    e.tmask = o.tmask;
+                    e.tval = o.tval;
+                    e.gmask = o.gmask;
+                    e.gval = o.gval;
+                    e.turns = o.ph.turns;
+                    if (pc == 0) {
+                        grp[5].push_back(e);
+                    } else {
+                        const int k = __builtin_ctz(o.rmask);
+                        if (o.rval) {
+                            grp[k].push_back(e);
+                        } else {  // f on bit k = 0:  f * (f^-1 on bit k = 1)
+                            grp[5].push_back(e);
+                            e.turns = 0u - e.turns;
+                            grp[k].push_back(e);
+                        }
+                    }
+                }
+                for (int g = 0; g < 6; ++g) {
+                    if (grp[g].empty()) continue;
+                    if (nent + (int)grp[g].size() > kTileMaxEntries || nout >= 2 * kTileMaxOps) {
+                        overflow = true;
+                        break;
+                    }
+                    TileOp &t = out[nout++];
+                    std::memset(&t, 0, sizeof t);
+                    t.kind = TOP_PHASES;
+                    t.k = (uint8_t)g;
+                    t.cond = 0xffff;
+                    t.first = (uint16_t)nent;
+                    t.count = (uint16_t)grp[g].size();
+                    for (const auto &e : grp[g]) P.entries[nent++] = e;
+                }
+                i = j;
+            }
+            if (overflow || nout > kTileMaxOps) {
+                // too large for one launch: plan this pass again with fewer gates
+                if (max_u2 <= 1 && max_ph <= 1) return ctx_fail(c, QK_EINVAL, "internal: tile program overflow");
+                max_u2 = std::max(1, max_u2 / 2);
+                max_ph = std::max(1, max_ph / 2);
+                continue;
+            }
+            std::memcpy(P.ops, out, sizeof(TileOp) * nout);
+            nops = nout;
+            P.nentries = nent;
         }
         P.nops = nops;
         P.store_arr = cur;
@@ -285,6 +367,8 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
         ctx_launch_end(tok);
         if (e != cudaSuccess) return ctx_fail(c, QK_ECUDA, cudaGetErrorString(e));
         rem.swap(left);
+        max_u2 = 100;
+        max_ph = 300;
     }
     return QK_OK;
 }

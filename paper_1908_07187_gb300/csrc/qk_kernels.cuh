@@ -112,14 +112,19 @@ struct RelabelArgs {
 // ---------------------------------------------------------------------------
 constexpr int kTileQubits = 13;
 constexpr int kTileThreads = 256;
-constexpr int kTileMaxOps = 256;
-constexpr int kTileMaxEntries = 640;
+constexpr int kTileMaxOps = 192;
+constexpr int kTileMaxEntries = 512;
+constexpr int kTileMaxMats = 160;
 constexpr int kTileMaxConds = 4;
 enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
 // TOP_PHASES: a group of diagonal terms that all add to one pending phase sum
 // (register bit k, or the constant when k == 5); each entry adds its turns when
 // its thread-bit and fixed-bit conditions hold.
-enum TileOpKind : uint8_t { TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_PHASES = 3 };
+// TOP_U2L: a layer of uncontrolled 2x2 gates on distinct register bits (k is
+// the bit mask); their matrices are mats[first...] in bit order.
+// TOP_PAIR: factor on the amplitudes whose register bits k and l are both 1
+// (code k | l << 3), under the op's thread / fixed-bit conditions.
+enum TileOpKind : uint8_t { TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_PHASES = 3, TOP_U2L = 4, TOP_PAIR = 5 };
 
 struct PhaseEntry {
     uint16_t tmask, tval;
@@ -133,9 +138,9 @@ struct TileOp {
     uint8_t rmask, rval;   // condition on register bits (5-bit register index space)
     uint16_t tmask, tval;  // condition on thread bits: bits 0..4 lane, 5..7 warp
     uint16_t cond;         // index into TileParams::conds, 0xffff = unconditional
-    uint16_t count;        // TOP_PHASES: entries [first, first + count)
-    uint16_t first;
-    uint16_t pad;
+    uint16_t count;        // TOP_PHASES: tile-uniform entries [first, first + count), then
+    uint16_t first;        //   count2 thread-dependent entries
+    uint16_t count2;
     uint64_t gmask, gval;  // condition on the tile's fixed (non-tile) physical bits
     union {
         float m[8];        // U2: m00, m01, m10, m11 as (re, im)
@@ -159,6 +164,7 @@ struct TileParams {
     int nentries;
     TileOp ops[kTileMaxOps];
     PhaseEntry entries[kTileMaxEntries];
+    float mats[kTileMaxMats][8];
 };
 static_assert(sizeof(TileParams) <= 32764, "tile program must fit in the kernel parameter space");
 

@@ -12,6 +12,8 @@
 // kernel, inserting a transpose when no ready gate fits the current one.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -20,10 +22,15 @@
 namespace qk {
 
 struct TilePlanner {
-    std::vector<int> scratch;
+    bool log = false;  // QK_PLAN_LOG=1: one line per tile pass on stderr
 };
 
-TilePlanner *make_planner() { return new TilePlanner(); }
+TilePlanner *make_planner() {
+    TilePlanner *p = new TilePlanner();
+    const char *e = std::getenv("QK_PLAN_LOG");
+    p->log = e && e[0] == '1';
+    return p;
+}
 void free_planner(TilePlanner *p) { delete p; }
 
 namespace {
@@ -116,7 +123,6 @@ void encode_cond(uint64_t mask, uint64_t val, int arr, const int *local_of, Tile
 }  // namespace
 
 qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> &ops) {
-    (void)planner;
     const int n = ctx_n(c);
     if (n < kTileQubits || ctx_prec(c) != 0) {
         for (const auto &op : ops) {
@@ -299,7 +305,25 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 }
                 int j = i;
                 while (j < nops && prog[j].kind == TOP_PHASE) ++j;
+                // per pending sum (register bit 0..4, constant 5): entries that add turns
                 std::vector<PhaseEntry> grp[6];
+                // terms on two register bits, reduced to the (1,1) pattern: key -> turns
+                struct PairKey {
+                    int code;
+                    uint16_t tmask, tval;
+                    uint64_t gmask, gval;
+                    uint32_t turns;
+                };
+                std::vector<PairKey> pairs;
+                auto add_entry = [&](int g, const TileOp &o, uint32_t turns) {
+                    PhaseEntry e;
+                    e.tmask = o.tmask;
+                    e.tval = o.tval;
+                    e.gmask = o.gmask;
+                    e.gval = o.gval;
+                    e.turns = turns;
+                    grp[g].push_back(e);
+                };
                 for (int t = i; t < j; ++t) {
                     const TileOp &o = prog[t];
                     if (nout >= 2 * kTileMaxOps) {
@@ -307,30 +331,71 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                         break;
                     }
                     const int pc = __builtin_popcount(o.rmask);
-                    if (o.cond != 0xffff || pc >= 2) {
+                    const uint32_t T = o.ph.turns;
+                    if (o.cond != 0xffff || pc >= 3) {
                         out[nout++] = o;   // applied directly
                         continue;
                     }
-                    PhaseEntry e;
-                    e.tmask = o.tmask;
-                    e.tval = o.tval;
-                    e.gmask = o.gmask;
-                    e.gval = o.gval;
-                    e.turns = o.ph.turns;
                     if (pc == 0) {
-                        grp[5].push_back(e);
-                    } else {
+                        add_entry(5, o, T);
+                    } else if (pc == 1) {
                         const int k = __builtin_ctz(o.rmask);
                         if (o.rval) {
-                            grp[k].push_back(e);
+                            add_entry(k, o, T);
                         } else {  // f on bit k = 0:  f * (f^-1 on bit k = 1)
-                            grp[5].push_back(e);
-                            e.turns = 0u - e.turns;
-                            grp[k].push_back(e);
+                            add_entry(5, o, T);
+                            add_entry(k, o, 0u - T);
                         }
+                    } else {
+                        // pattern (vk, vl) on register bits k < l as exact sums of a constant,
+                        // single-bit terms and a (1,1) pair term
+                        const int k = __builtin_ctz(o.rmask), l = 31 - __builtin_clz(o.rmask);
+                        const int vk = (o.rval >> k) & 1, vl = (o.rval >> l) & 1;
+                        uint32_t pair = T;
+                        if (vk && !vl) {
+                            add_entry(k, o, T);
+                            pair = 0u - T;
+                        } else if (!vk && vl) {
+                            add_entry(l, o, T);
+                            pair = 0u - T;
+                        } else if (!vk && !vl) {
+                            add_entry(5, o, T);
+                            add_entry(k, o, 0u - T);
+                            add_entry(l, o, 0u - T);
+                        }
+                        const int code = k | (l << 3);
+                        bool merged = false;
+                        for (auto &pk : pairs)
+                            if (pk.code == code && pk.tmask == o.tmask && pk.tval == o.tval && pk.gmask == o.gmask &&
+                                pk.gval == o.gval) {
+                                pk.turns += pair;
+                                merged = true;
+                                break;
+                            }
+                        if (!merged) pairs.push_back({code, o.tmask, o.tval, o.gmask, o.gval, pair});
                     }
                 }
-                for (int g = 0; g < 6; ++g) {
+                for (const auto &pk : pairs) {
+                    if (pk.turns == 0) continue;
+                    if (nout >= 2 * kTileMaxOps) {
+                        overflow = true;
+                        break;
+                    }
+                    TileOp &t = out[nout++];
+                    std::memset(&t, 0, sizeof t);
+                    t.kind = TOP_PAIR;
+                    t.k = (uint8_t)pk.code;
+                    t.tmask = pk.tmask;
+                    t.tval = pk.tval;
+                    t.gmask = pk.gmask;
+                    t.gval = pk.gval;
+                    t.cond = 0xffff;
+                    const double ang = 2.0 * M_PI * (double)pk.turns / 4294967296.0;
+                    t.ph.re = (float)std::cos(ang);
+                    t.ph.im = (float)std::sin(ang);
+                    t.ph.turns = pk.turns;
+                }
+                for (int g = 0; g < 6 && !overflow; ++g) {
                     if (grp[g].empty()) continue;
                     if (nent + (int)grp[g].size() > kTileMaxEntries || nout >= 2 * kTileMaxOps) {
                         overflow = true;
@@ -342,8 +407,14 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                     t.k = (uint8_t)g;
                     t.cond = 0xffff;
                     t.first = (uint16_t)nent;
-                    t.count = (uint16_t)grp[g].size();
-                    for (const auto &e : grp[g]) P.entries[nent++] = e;
+                    // tile-uniform entries first (no thread-bit condition), then the rest
+                    int nu = 0;
+                    for (const auto &e : grp[g])
+                        if (e.tmask == 0) { P.entries[nent++] = e; ++nu; }
+                    for (const auto &e : grp[g])
+                        if (e.tmask != 0) P.entries[nent++] = e;
+                    t.count = (uint16_t)nu;
+                    t.count2 = (uint16_t)(grp[g].size() - nu);
                 }
                 i = j;
             }
@@ -354,18 +425,82 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 max_ph = std::max(1, max_ph / 2);
                 continue;
             }
-            std::memcpy(P.ops, out, sizeof(TileOp) * nout);
-            nops = nout;
+            // merge runs of consecutive uncontrolled 2x2 gates on distinct
+            // register bits into layer ops (they commute with each other)
+            int nfin = 0, nmat = 0;
+            for (int i = 0; i < nout && !overflow;) {
+                const TileOp &o = out[i];
+                const bool plain_u2 = o.kind == TOP_U2 && o.rmask == 0 && o.tmask == 0 && o.gmask == 0 &&
+                                      o.cond == 0xffff;
+                if (!plain_u2) {
+                    if (nfin >= kTileMaxOps) { overflow = true; break; }
+                    P.ops[nfin++] = out[i++];
+                    continue;
+                }
+                int bits = 0, j = i;
+                while (j < nout) {
+                    const TileOp &q = out[j];
+                    const bool ok = q.kind == TOP_U2 && q.rmask == 0 && q.tmask == 0 && q.gmask == 0 &&
+                                    q.cond == 0xffff && !(bits & (1 << q.k));
+                    if (!ok) break;
+                    bits |= 1 << q.k;
+                    ++j;
+                }
+                if (nfin >= kTileMaxOps || nmat + (j - i) > kTileMaxMats) { overflow = true; break; }
+                TileOp &t = P.ops[nfin++];
+                std::memset(&t, 0, sizeof t);
+                t.kind = TOP_U2L;
+                t.k = (uint8_t)bits;
+                t.cond = 0xffff;
+                t.first = (uint16_t)nmat;
+                t.count = (uint16_t)(j - i);
+                // matrices stored in register-bit order
+                for (int b = 0; b < 5; ++b)
+                    for (int q = i; q < j; ++q)
+                        if (out[q].k == b) std::memcpy(P.mats[nmat++], out[q].m, sizeof(float) * 8);
+                i = j;
+            }
+            if (overflow) {
+                if (max_u2 <= 1 && max_ph <= 1) return ctx_fail(c, QK_EINVAL, "internal: tile program overflow");
+                max_u2 = std::max(1, max_u2 / 2);
+                max_ph = std::max(1, max_ph / 2);
+                continue;
+            }
+            nops = nfin;
             P.nentries = nent;
         }
         P.nops = nops;
         P.store_arr = cur;
+        if (planner->log) {
+            int cnt_k[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int i = 0; i < nops; ++i) cnt_k[P.ops[i].kind]++;
+            std::fprintf(stderr,
+                         "[qk plan] pass S=%#llx gates=%d (u2 %d, phase %d) ops=%d u2=%d layers=%d phase_direct=%d "
+                         "phase_groups=%d entries=%d pairs=%d xpose=%d store_arr=%d\n",
+                         (unsigned long long)S, m, n_u2, n_ph, nops, cnt_k[TOP_U2], cnt_k[TOP_U2L], cnt_k[TOP_PHASE],
+                         cnt_k[TOP_PHASES], P.nentries, cnt_k[TOP_PAIR], cnt_k[TOP_XPOSE], cur);
+        }
 
         void *tok = nullptr;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (planner->log) {  // trace mode: time this pass on its own (synchronous)
+            cudaEventCreate(&ev0);
+            cudaEventCreate(&ev1);
+            cudaEventRecord(ev0, ctx_stream(c));
+        }
         ctx_launch_begin(c, 0, 2.0 * 8.0 * (double)(1ull << n), &tok);
         cudaError_t e = launch_tile(ctx_state(c), P, ctx_cbits(c), ctx_stream(c));
         ctx_launch_end(tok);
         if (e != cudaSuccess) return ctx_fail(c, QK_ECUDA, cudaGetErrorString(e));
+        if (planner->log) {
+            float ms = 0.f;
+            cudaEventRecord(ev1, ctx_stream(c));
+            cudaEventSynchronize(ev1);
+            cudaEventElapsedTime(&ms, ev0, ev1);
+            std::fprintf(stderr, "[qk plan]   %.3f ms\n", ms);
+            cudaEventDestroy(ev0);
+            cudaEventDestroy(ev1);
+        }
         rem.swap(left);
         max_u2 = 100;
         max_ph = 300;

@@ -344,3 +344,25 @@ def test_fused_matches_plain_and_uses_few_passes(qk, n):
         ctx.close()
     assert np.max(np.abs(got["fused"][0] - got["plain"][0])) < 1e-4
     assert got["fused"][1]["launches"] < got["plain"][1]["launches"] / 10
+
+
+@pytest.mark.parametrize("targets", [(5, 6), (0, 9), (2, 13), (14, 3), (11, 12)])
+def test_fused_two_qubit_diagonals_every_pattern(qk, targets):
+    """Diagonal 2-qubit gates whose non-unit entries sit on the (0,0), (0,1),
+    (1,0) and (1,1) patterns, between non-diagonal gates on the same qubits."""
+    n = 15
+    psi = workloads.random_state(n, 77 + sum(targets))
+    ctx = new_ctx(qk, n, "c64", "fused", psi)
+    ref = oracle.OracleState(n, psi=psi)
+    diags = [np.diag(np.exp(1j * np.array(a))) for a in ([0.7, 0, 0, -1.1], [0, 0.4, 1.3, 0], [0, 2.0, 0, 0],
+                                                         [0, 0, -0.6, 0], [math.pi, 0, 0, 0])]
+    for D in diags:
+        gid = ctx.define_gate_matrix(D)
+        ctx.apply_gate(gid, targets)
+        ref.apply_matrix(D, targets)
+        ctx.apply_gate("h", [targets[0]])
+        ref.apply_matrix(oracle.GATES_1Q["h"], [targets[0]])
+        ctx.apply_gate("u3", [targets[1]], params=[0.3, 0.9, 1.7])
+        ref.apply_matrix(oracle.u3(0.3, 0.9, 1.7), [targets[1]])
+    check_state(ctx.get_state(), ref.psi, "c64")
+    ctx.close()

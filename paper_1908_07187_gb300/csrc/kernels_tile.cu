@@ -6,11 +6,12 @@
 // one read + one write of the state however many gates it carries.
 //
 // Each of the 256 threads holds 32 amplitudes in registers, split into real and
-// imaginary parts and packed two amplitudes per 64-bit register pair
-// (re[2j], re[2j+1]) / (im[2j], im[2j+1]), so that a 2x2 gate on register bit
-// k >= 1 runs on Blackwell's paired FP32 instructions (two lanes of math per
-// instruction).  The register bits are changed by transposing the tile through
-// shared memory (three fixed arrangements, see qk_kernels.cuh).
+// imaginary parts, two amplitudes per float2 (re[2j], re[2j+1]) /
+// (im[2j], im[2j+1]).  A 2x2 gate on a register bit is a set of 16 butterflies
+// between registers of the same thread (scalar FP32 FMAs: the paired f32x2 forms
+// measured slower in this register-bound loop).  The register bits are changed
+// by transposing the tile through shared memory (three fixed arrangements, see
+// qk_kernels.cuh).
 //
 // Diagonal gates are not applied one by one: each thread keeps a pending
 // diagonal D(r) = exp(2 pi i (t0 + sum_{k in r} t_k) / 2^32) as six 32-bit
@@ -129,8 +130,8 @@ struct Mat {
     }
 };
 
-// 2x2 gate on register bit K >= 1: couples (j, j | 2^(K-1)) of packed registers,
-// two amplitude pairs per instruction.  A couple acts if (2j & rmask) == rmask;
+// 2x2 gate on register bit K >= 1: couples (j, j | 2^(K-1)) of float2 registers,
+// two amplitude pairs per couple.  A couple acts if (2j & rmask) == rmask;
 // with register bit 0 in rmask only the odd halves act (the even halves keep
 // their old values).
 template <int K>

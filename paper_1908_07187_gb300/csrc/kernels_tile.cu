@@ -282,6 +282,52 @@ struct Pending {
     }
 };
 
+// One gate of a TOP_U2L layer on register bit K: fold the pending phase of bit
+// K into the matrix, then the butterflies.
+template <int K>
+__device__ __forceinline__ void layer_gate(Regs &v, Pending &pd, const float *m) {
+    float2 m00 = make_float2(m[0], m[1]), m01 = make_float2(m[2], m[3]);
+    float2 m10 = make_float2(m[4], m[5]), m11 = make_float2(m[6], m[7]);
+    if ((pd.mask & (1 << K)) && pd.t[K] != 0) {
+        const float2 ak = turns_to_phase(pd.t[K]);
+        m01 = cmul(m01, ak);
+        m11 = cmul(m11, ak);
+    }
+    pd.t[K] = 0;
+    pd.mask &= ~(1 << K);
+    if constexpr (K == 0) {
+        u2_bit0(v, m00, m01, m10, m11, 0);
+    } else {
+        const Mat M(m00, m01, m10, m11);
+        u2_packed<K>(v, M, 0);
+    }
+}
+
+// amplitudes whose register bits K and L are both 1 are multiplied by f (or negated)
+template <int K, int L, int r>
+__device__ __forceinline__ void pair_one(Regs &v, float2 f, bool neg) {
+    if constexpr (((r >> K) & 1) && ((r >> L) & 1)) {
+        float &x = re_of<r>(v);
+        float &y = im_of<r>(v);
+        if (neg) {
+            x = -x;
+            y = -y;
+        } else {
+            const float xr = x, xi = y;
+            x = xr * f.x - xi * f.y;
+            y = xr * f.y + xi * f.x;
+        }
+    }
+}
+template <int K, int L, int... rs>
+__device__ __forceinline__ void pair_all(Regs &v, float2 f, bool neg, std::integer_sequence<int, rs...>) {
+    (pair_one<K, L, rs>(v, f, neg), ...);
+}
+template <int K, int L>
+__device__ __forceinline__ void pair_factor(Regs &v, float2 f, bool neg) {
+    pair_all<K, L>(v, f, neg, std::make_integer_sequence<int, 32>{});
+}
+
 __device__ __forceinline__ bool op_applies(const TileOp &op, int tbits, uint64_t base, unsigned condok) {
     if ((tbits & op.tmask) != op.tval) return false;
     if ((base & op.gmask) != op.gval) return false;
@@ -359,10 +405,28 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                 cur = op.k;
                 continue;
             }
-            if (op.kind == TOP_PHASES) {  // branch-free sum of the group's active terms
+            if (op.kind == TOP_U2L) {
+                const float *mp = P.mats[op.first];
+                const int bits = op.k;
+                if (bits & 1) { layer_gate<0>(v, pd, mp); mp += 8; }
+                if (bits & 2) { layer_gate<1>(v, pd, mp); mp += 8; }
+                if (bits & 4) { layer_gate<2>(v, pd, mp); mp += 8; }
+                if (bits & 8) { layer_gate<3>(v, pd, mp); mp += 8; }
+                if (bits & 16) layer_gate<4>(v, pd, mp);
+                continue;
+            }
+            if (op.kind == TOP_PHASES) {
+                // tile-uniform terms: the 32 lanes share them out, then an integer sum
                 uint32_t acc = 0;
-                const int end = op.first + op.count;
-                for (int e = op.first; e < end; ++e) {
+                const int endu = op.first + op.count;
+                for (int e = op.first + lane; e < endu; e += 32) {
+                    const PhaseEntry &pe = P.entries[e];
+                    acc += ((base & pe.gmask) == pe.gval) ? pe.turns : 0u;
+                }
+                if (op.count) acc = __reduce_add_sync(0xffffffffu, acc);
+                // terms that depend on the thread: each thread sums its own
+                const int endt = endu + op.count2;
+                for (int e = endu; e < endt; ++e) {
                     const PhaseEntry &pe = P.entries[e];
                     const bool on = ((tbits & pe.tmask) == pe.tval) & ((base & pe.gmask) == pe.gval);
                     acc += on ? pe.turns : 0u;
@@ -376,6 +440,23 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                 continue;
             }
             if (!op_applies(op, tbits, base, condok)) continue;
+            if (op.kind == TOP_PAIR) {
+                const float2 f = make_float2(op.ph.re, op.ph.im);
+                const bool neg = op.ph.turns == 0x80000000u;
+                switch (op.k) {
+                    case 0 | (1 << 3): pair_factor<0, 1>(v, f, neg); break;
+                    case 0 | (2 << 3): pair_factor<0, 2>(v, f, neg); break;
+                    case 0 | (3 << 3): pair_factor<0, 3>(v, f, neg); break;
+                    case 0 | (4 << 3): pair_factor<0, 4>(v, f, neg); break;
+                    case 1 | (2 << 3): pair_factor<1, 2>(v, f, neg); break;
+                    case 1 | (3 << 3): pair_factor<1, 3>(v, f, neg); break;
+                    case 1 | (4 << 3): pair_factor<1, 4>(v, f, neg); break;
+                    case 2 | (3 << 3): pair_factor<2, 3>(v, f, neg); break;
+                    case 2 | (4 << 3): pair_factor<2, 4>(v, f, neg); break;
+                    default: pair_factor<3, 4>(v, f, neg); break;
+                }
+                continue;
+            }
             if (op.kind == TOP_U2) {
                 float2 m00 = make_float2(op.m[0], op.m[1]), m01 = make_float2(op.m[2], op.m[3]);
                 float2 m10 = make_float2(op.m[4], op.m[5]), m11 = make_float2(op.m[6], op.m[7]);
@@ -404,7 +485,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                         default: u2_packed<4>(v, M, op.rmask); break;
                     }
                 }
-            } else {  // TOP_PHASE: factor where (register index & rmask) == rval
+            } else if (op.kind == TOP_PHASE) {  // factor where (register index & rmask) == rval
                 const int rm = op.rmask;
                 const int pc = __popc(rm);
                 if (pc == 0) {

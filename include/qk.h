@@ -176,6 +176,20 @@ qk_status qk_apply_gate(qk_ctx *ctx, int gate_id, const int *targets, int nt,
  * the device from the cbit values (no host round trip).  ncb <= 62. */
 qk_status qk_apply_rphase_cbits(qk_ctx *ctx, int target, const int *cbits, int ncb);
 
+/* One stage of Kitaev's one-control-qubit order finding (Shor section, Fig. 2b
+ * and Fig. 6b; the nx2n command script of Appendix A), fused: H(control); the
+ * permutation gate perm_gate_id (from qk_define_gate_perm_mulmod or _table) on
+ * targets[0..nt-1] controlled by `control`; the phase correction of
+ * qk_apply_rphase_cbits(control, phase_cbits, ncb); H(control); measure
+ * `control` with `uniform` into dest_cbit; X(control) if the outcome is 1.
+ * Precondition: `control` is |0> (every amplitude with the control bit set is
+ * zero), which holds at the start and after every stage.  The result equals the
+ * six separate calls; the stage costs two passes over the control = 0 half
+ * plus a one-block decision.  Stream-ordered, no host round trip.
+ * Errors: QK_EINVAL (bad ids, lists or uniform), QK_ENOMEM, QK_ECUDA. */
+qk_status qk_apply_kitaev_stage(qk_ctx *ctx, int control, int perm_gate_id, const int *targets, int nt,
+                                const int *phase_cbits, int ncb, double uniform, int dest_cbit);
+
 /* "Measure" (Q-Kit section, command 3) with "Copy" into classical bits:
  * measures qubits[0..nq-1] one after another in list order.  For each, P0 is the
  * probability of reading 0 (summed in FP64 on the device), the outcome is

@@ -759,6 +759,61 @@ qk_status qk_apply_rphase_cbits(qk_ctx *c, int target, const int *cbits, int ncb
     return QK_OK;
 }
 
+qk_status qk_apply_kitaev_stage(qk_ctx *c, int control, int gate_id, const int *targets, int nt,
+                                const int *phase_cbits, int ncb, double uniform, int dest) {
+    if (!c) return QK_EINVAL;
+    if (c->n < 2) return fail(c, QK_ESTATE, "kitaev_stage: need at least 2 qubits");
+    if (control < 0 || control >= c->n) return fail(c, QK_EINVAL, "kitaev_stage: bad control qubit");
+    if (gate_id < 0 || gate_id >= (int)c->gates.size() || c->gates[gate_id].kind == 0)
+        return fail(c, QK_EINVAL, "kitaev_stage: gate %d is not a permutation gate", gate_id);
+    const GateDef &g = c->gates[gate_id];
+    if (nt != g.k || !valid_qubits(c, targets, nt)) return fail(c, QK_EINVAL, "kitaev_stage: bad target list");
+    for (int a = 0; a < nt; ++a)
+        if (targets[a] == control) return fail(c, QK_EINVAL, "kitaev_stage: control is a target");
+    if (ncb < 0 || ncb > QK_MAX_RPHASE_CBITS || (ncb > 0 && !phase_cbits))
+        return fail(c, QK_EINVAL, "kitaev_stage: bad phase cbit list");
+    for (int a = 0; a < ncb; ++a)
+        if (phase_cbits[a] < 0 || phase_cbits[a] >= c->ncb) return fail(c, QK_EINVAL, "kitaev_stage: cbit out of range");
+    if (!(uniform >= 0.0 && uniform < 1.0)) return fail(c, QK_EINVAL, "kitaev_stage: uniform not in [0, 1)");
+    if (dest < 0 || dest >= c->ncb) return fail(c, QK_EINVAL, "kitaev_stage: destination cbit out of range");
+    qk_status s = flush(c);
+    if (s != QK_OK) return s;
+    s = ensure_scratch(c);
+    if (s != QK_OK) return s;
+    s = ensure_slots(c, 1);
+    if (s != QK_OK) return s;
+    qk::KitaevArgs a{};
+    a.cpos = c->l2p[control];
+    a.w = g.k;
+    for (int t = 0; t < g.k; ++t) a.rpos[t] = c->l2p[targets[t]];
+    a.kind = g.kind == 1 ? 0 : 1;
+    a.N = g.N;
+    a.cinv = g.cinv;
+    a.mu = g.kind == 1 ? (~0ull) / g.N : 0;
+    a.finv = g.d_finv;
+    a.n_rphase = ncb;
+    for (int l = 0; l < ncb; ++l) a.rphase_idx[l] = phase_cbits[l];
+    a.n_half = 1ull << (c->n - 1);
+    const double half = (double)c->amp * (double)a.n_half;
+    {
+        LaunchScope ls(c, 4, 2 * half);
+        CUDA_TRY(c, qk::launch_kitaev_reduce((int)c->prec, c->d_state, a, c->d_cbits, c->d_partials, c->meas_blocks,
+                                             c->stream));
+    }
+    {
+        LaunchScope ls(c, 6, 0);
+        CUDA_TRY(c, qk::launch_measure_decide(c->d_partials, c->meas_blocks, uniform, c->d_slots, c->d_cbits, dest,
+                                              c->stream));
+    }
+    {
+        LaunchScope ls(c, 4, 4 * half);
+        CUDA_TRY(c, qk::launch_kitaev_update((int)c->prec, c->d_state, c->d_scratch, a, c->d_cbits, c->d_slots, c->sms,
+                                             c->stream));
+    }
+    std::swap(c->d_state, c->d_scratch);
+    return QK_OK;
+}
+
 qk_status qk_measure(qk_ctx *c, const int *qubits, int nq, const double *uniforms, const int *dest, uint64_t *outcome) {
     if (!c) return QK_EINVAL;
     if (c->n == 0) return fail(c, QK_ESTATE, "measure: no qubits");

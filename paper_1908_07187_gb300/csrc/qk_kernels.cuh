@@ -91,6 +91,21 @@ struct MeasArgs {
     uint64_t n_units;     // 2^(n-k) amplitudes match the prefix
 };
 
+// One fused Kitaev stage (kernels_kitaev.cu): control qubit at physical bit
+// cpos, register of w qubits at rpos[] (rpos[0] = MSB), permutation f given by
+// its inverse (mul-mod: cinv, N, mu; table: finv), phase from cbits.
+struct KitaevArgs {
+    int cpos;
+    int w;
+    int rpos[kMaxPermW];
+    int kind;             // 0 = mul-mod, 1 = table
+    uint64_t N, cinv, mu;
+    const uint32_t *finv;
+    int n_rphase;
+    int rphase_idx[kMaxRphase];
+    uint64_t n_half;      // 2^(n-1): amplitudes with the control bit 0
+};
+
 // Qubit-relabelling gather: out[logical index] = in[physical index].
 struct RelabelArgs {
     int n;
@@ -187,6 +202,10 @@ cudaError_t launch_measure_decide(const double *partials, int nblocks, double u,
                                   uint8_t *cbits, int dest, cudaStream_t s);
 cudaError_t launch_measure_collapse(int prec, void *psi, int n, const MeasArgs &a, const MeasSlot *slots, int sms,
                                     cudaStream_t s);
+cudaError_t launch_kitaev_reduce(int prec, const void *psi, const KitaevArgs &a, const uint8_t *cbits,
+                                 double *partials, int nblocks, cudaStream_t s);
+cudaError_t launch_kitaev_update(int prec, const void *psi, void *out, const KitaevArgs &a, const uint8_t *cbits,
+                                 const MeasSlot *slot, int sms, cudaStream_t s);
 cudaError_t launch_set_basis(int prec, void *psi, uint64_t index, cudaStream_t s);
 cudaError_t launch_relabel(int prec, const void *in, void *out, const RelabelArgs &a, int sms,
                            cudaStream_t s);

@@ -58,6 +58,8 @@ _SIGS = {
     "qk_apply_gate": ([_P, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int, _DP,
                        ctypes.c_int], ctypes.c_int),
     "qk_apply_rphase_cbits": ([_P, ctypes.c_int, _IP, ctypes.c_int], ctypes.c_int),
+    "qk_apply_kitaev_stage": ([_P, ctypes.c_int, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int,
+                               ctypes.c_double, ctypes.c_int], ctypes.c_int),
     "qk_measure": ([_P, _IP, ctypes.c_int, _DP, _IP, _U64P], ctypes.c_int),
     "qk_read_cbits": ([_P, _U8P, ctypes.c_int], ctypes.c_int),
     "qk_write_cbits": ([_P, ctypes.c_int, _U8P, ctypes.c_int], ctypes.c_int),
@@ -202,6 +204,12 @@ class Context:
         cb, n = _ints(cbits)
         self._check(_lib.qk_apply_rphase_cbits(self._h, target, cb, n))
 
+    def apply_kitaev_stage(self, control: int, perm_gate: int, targets: Sequence[int], phase_cbits: Sequence[int],
+                           uniform: float, dest_cbit: int):
+        t, nt = _ints(targets)
+        cb, ncb = _ints(phase_cbits)
+        self._check(_lib.qk_apply_kitaev_stage(self._h, control, perm_gate, t, nt, cb, ncb, uniform, dest_cbit))
+
     def measure(self, qubits: Sequence[int], uniforms: Sequence[float], dest: Optional[Sequence[int]] = None,
                 wait: bool = True) -> Optional[int]:
         q, nq = _ints(qubits)
@@ -312,3 +320,29 @@ def run_circuit(circ, precision: str = "c64", exec_mode: str = "fused", **kw) ->
         ctx.add_cbits(circ.n_cbits)
     run_ops(ctx, circ.ops)
     return ctx
+
+
+def run_kitaev_fused(ctx: Context, circ) -> None:
+    """Marshal a workloads.kitaev_circuit into one qk_apply_kitaev_stage call per
+    stage (the op list must have the H / mulmod / rphase / H / measure / X shape
+    that workloads.kitaev_circuit writes)."""
+    ops = circ.ops
+    i = 0
+    if ops[0].kind == "x" and not ops[0].cond:  # work register initialisation
+        ctx.apply_gate("x", ops[0].targets)
+        i = 1
+    while i < len(ops):
+        h, mm = ops[i], ops[i + 1]
+        has_phase = ops[i + 2].kind == "rphase"
+        ph = ops[i + 2] if has_phase else None
+        k = i + 3 if has_phase else i + 2
+        meas = ops[k + 1]
+        if h.kind != "h" or mm.kind != "mulmod" or ops[k].kind != "h" or meas.kind != "measure" or \
+                ops[k + 2].kind != "x":
+            raise ValueError("op list is not a sequence of Kitaev stages")
+        a, j, N = (int(x) for x in mm.params)
+        gid = ctx.define_gate_perm_mulmod(len(mm.targets), pow(a, 1 << j, N), N)
+        ctx.apply_kitaev_stage(h.targets[0], gid, mm.targets, ph.cbits if ph else (), meas.uniforms[0],
+                               meas.cbits[0])
+        i = k + 3
+

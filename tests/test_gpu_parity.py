@@ -366,3 +366,37 @@ def test_fused_two_qubit_diagonals_every_pattern(qk, targets):
         ref.apply_matrix(oracle.u3(0.3, 0.9, 1.7), [targets[1]])
     check_state(ctx.get_state(), ref.psi, "c64")
     ctx.close()
+
+
+@pytest.mark.parametrize("b,prec", [(4, "c64"), (6, "c128"), (12, "c64"), (14, "c64")])
+def test_fused_kitaev_stage_matches_oracle_and_generic(qk, b, prec):
+    N, a = (15, 7) if b == 4 else workloads.kitaev_parameters(b, seed=3)
+    circ = workloads.kitaev_circuit(N, a, seed=21)
+    ref = oracle.run_circuit(circ)
+    ctx = qk.Context(prec, "fused")
+    ctx.add_qubits(circ.n_qubits)
+    ctx.add_cbits(circ.n_cbits)
+    qk.run_kitaev_fused(ctx, circ)
+    assert list(ctx.read_cbits()) == [int(x) for x in ref.cbits]
+    check_state(ctx.get_state(), ref.psi, prec)
+    gen = qk.run_circuit(circ, prec, "fused")
+    np.testing.assert_allclose(ctx.get_state(), gen.get_state(), atol=TOL[prec])
+    ctx.close()
+    gen.close()
+
+
+def test_fused_kitaev_stage_rejects_bad_arguments(qk):
+    ctx = qk.Context("c64", "fused")
+    ctx.add_qubits(5)
+    ctx.add_cbits(2)
+    gid = ctx.define_gate_perm_mulmod(4, 7, 15)
+    u = ctx.define_gate_matrix(np.eye(2))
+    with pytest.raises(qk.QKError):
+        ctx.apply_kitaev_stage(0, u, [1, 2, 3, 4], [], 0.5, 0)        # not a permutation gate
+    with pytest.raises(qk.QKError):
+        ctx.apply_kitaev_stage(1, gid, [1, 2, 3, 4], [], 0.5, 0)      # control among the targets
+    with pytest.raises(qk.QKError):
+        ctx.apply_kitaev_stage(0, gid, [1, 2, 3, 4], [5], 0.5, 0)     # cbit out of range
+    with pytest.raises(qk.QKError):
+        ctx.apply_kitaev_stage(0, gid, [1, 2, 3, 4], [], 1.0, 0)      # uniform outside [0, 1)
+    ctx.close()

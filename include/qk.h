@@ -234,6 +234,24 @@ qk_status qk_sync(qk_ctx *ctx);
 int qk_num_qubits(const qk_ctx *ctx);
 int qk_num_cbits(const qk_ctx *ctx);
 
+/* CUDA-graph capture of a sequence of calls (no counterpart in the paper; it
+ * replaces a host loop of launches, e.g. a whole Kitaev order-finding run, by one
+ * graph launch).  qk_capture_begin flushes queued gates, undoes qubit
+ * relabelling, and starts capturing the context's stream.  Between begin and end
+ * only stream-ordered calls are allowed (gates, stages, measurements without an
+ * outcome, qk_reset, qk_flush); calls that allocate or wait return QK_ESTATE, so
+ * define gates and apply one permutation (which allocates its gather buffer)
+ * before capturing.  qk_capture_end flushes, restores the qubit map and the
+ * state's buffer inside the capture (so that every replay starts and ends in the
+ * same buffer with the same map), ends the capture and instantiates the graph.
+ * Gate parameters and uniforms are fixed at capture time. */
+typedef struct qk_graph qk_graph;
+qk_status qk_capture_begin(qk_ctx *ctx);
+qk_status qk_capture_end(qk_ctx *ctx, qk_graph **out);
+/* Replay the graph on its context's stream (stream-ordered, does not wait). */
+qk_status qk_graph_launch(qk_graph *g);
+qk_status qk_graph_destroy(qk_graph *g);
+
 /* Counters since creation or the last reset_counters: kernel launches, passes
  * over the state (launches that stream the full state), and algorithmic bytes
  * (2^n * amplitude size * 2 per full pass, read + write). */

@@ -79,7 +79,16 @@ struct qk_ctx {
     double prof_ms[QK_NUM_LAUNCH_CLASSES] = {};
     double prof_bytes[QK_NUM_LAUNCH_CLASSES] = {};
 
+    bool capturing = false;       // the stream is being captured into a CUDA graph
+    void *cap_state0 = nullptr;   // state buffer when the capture began
+
     std::string err;
+};
+
+struct qk_graph {
+    qk_ctx *ctx;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
 };
 
 namespace {
@@ -121,7 +130,7 @@ struct LaunchScope {
     double bytes;
     cudaEvent_t a = nullptr;
     LaunchScope(qk_ctx *c_, int cls_, double bytes_) : c(c_), cls(cls_), bytes(bytes_) {
-        if (c->opt.profile) {
+        if (c->opt.profile && !c->capturing) {
             a = get_event(c);
             cudaEventRecord(a, c->stream);
         }
@@ -131,13 +140,18 @@ struct LaunchScope {
         c->alg_bytes += bytes;
         const double fp = (double)full_pass_bytes(c);
         if (fp > 0) c->passes_x1000 += (uint64_t)llround(1000.0 * bytes / fp);
-        if (c->opt.profile) {
+        if (c->opt.profile && !c->capturing) {
             cudaEvent_t b = get_event(c);
             cudaEventRecord(b, c->stream);
             c->prof.push_back({cls, a, b, bytes});
         }
     }
 };
+
+#define NOT_WHILE_CAPTURING(c, what)                                                   \
+    do {                                                                               \
+        if ((c)->capturing) return fail((c), QK_ESTATE, "%s is not allowed while capturing", what); \
+    } while (0)
 
 bool valid_qubits(const qk_ctx *c, const int *q, int k) {
     if (k < 0 || (k > 0 && !q)) return false;
@@ -322,6 +336,7 @@ qk_status apply_1q(qk_ctx *c, const cd m[4], int q, uint64_t cmask, const qk::Co
 
 qk_status ensure_scratch(qk_ctx *c) {
     if (c->d_scratch && c->scratch_bytes == c->state_bytes) return QK_OK;
+    if (c->capturing) return fail(c, QK_ESTATE, "a gather buffer would be allocated during capture");
     if (c->d_scratch) cudaFree(c->d_scratch);
     c->d_scratch = nullptr;
     c->scratch_bytes = 0;
@@ -357,6 +372,7 @@ qk_status canonicalize(qk_ctx *c) {
 
 qk_status ensure_slots(qk_ctx *c, int nq) {
     if (nq <= c->slot_cap) return QK_OK;
+    if (c->capturing) return fail(c, QK_ESTATE, "measurement slots would be allocated during capture");
     if (c->d_slots) cudaFree(c->d_slots);
     c->d_slots = nullptr;
     int cap = std::max(nq, 64);
@@ -471,6 +487,7 @@ qk_status qk_destroy(qk_ctx *c) {
 
 qk_status qk_add_qubits(qk_ctx *c, int k, int *first) {
     if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "add_qubits");
     if (k < 1 || c->n + k > QK_MAX_QUBITS) return fail(c, QK_EINVAL, "add_qubits: bad count %d (have %d)", k, c->n);
     qk_status s = flush(c);
     if (s != QK_OK) return s;
@@ -508,6 +525,7 @@ qk_status qk_add_qubits(qk_ctx *c, int k, int *first) {
 
 qk_status qk_add_cbits(qk_ctx *c, int k, int *first) {
     if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "add_cbits");
     if (k < 1 || c->ncb + k > (1 << 20)) return fail(c, QK_EINVAL, "add_cbits: bad count %d", k);
     if (c->ncb + k > c->cb_cap) {
         int cap = std::max(c->ncb + k, std::max(64, 2 * c->cb_cap));
@@ -529,6 +547,7 @@ qk_status qk_add_cbits(qk_ctx *c, int k, int *first) {
 
 qk_status qk_define_gate_matrix(qk_ctx *c, int k, const double *u, double tol, int *gate_id) {
     if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "define_gate_matrix");
     if (k < 1 || k > QK_MAX_MATRIX_QUBITS || !u || !gate_id || !(tol >= 0))
         return fail(c, QK_EINVAL, "define_gate_matrix: bad arguments");
     const int d = 1 << k;
@@ -571,6 +590,7 @@ static uint64_t modinv(uint64_t a, uint64_t N, bool &ok) {
 
 qk_status qk_define_gate_perm_mulmod(qk_ctx *c, int w, uint64_t cc, uint64_t N, int *gate_id) {
     if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "define_gate_perm_mulmod");
     if (w < 1 || w > QK_MAX_PERM_QUBITS || !gate_id || N < 2 || N > (1ull << w))
         return fail(c, QK_EINVAL, "define_gate_perm_mulmod: bad w=%d or N=%llu", w, (unsigned long long)N);
     if (cc >= N) return fail(c, QK_EINVAL, "define_gate_perm_mulmod: c must be < N");
@@ -591,6 +611,7 @@ qk_status qk_define_gate_perm_mulmod(qk_ctx *c, int w, uint64_t cc, uint64_t N, 
 
 qk_status qk_define_gate_perm_table(qk_ctx *c, int w, const uint64_t *f, int *gate_id) {
     if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "define_gate_perm_table");
     if (w < 1 || w > 24 || !f || !gate_id) return fail(c, QK_EINVAL, "define_gate_perm_table: bad arguments");
     const uint64_t d = 1ull << w;
     std::vector<uint32_t> inv(d, 0xffffffffu);
@@ -823,6 +844,7 @@ qk_status qk_measure(qk_ctx *c, const int *qubits, int nq, const double *uniform
         if (!(uniforms[a] >= 0.0 && uniforms[a] < 1.0)) return fail(c, QK_EINVAL, "measure: uniform %d not in [0, 1)", a);
         if (dest && (dest[a] < 0 || dest[a] >= c->ncb)) return fail(c, QK_EINVAL, "measure: destination cbit %d out of range", dest[a]);
     }
+    if (outcome && c->capturing) return fail(c, QK_ESTATE, "measure with a host outcome is not allowed while capturing");
     qk_status s = flush(c);
     if (s != QK_OK) return s;
     s = ensure_slots(c, nq);
@@ -854,6 +876,7 @@ qk_status qk_measure(qk_ctx *c, const int *qubits, int nq, const double *uniform
         LaunchScope ls(c, 5, (double)c->amp * (double)((1ull << c->n) + (1ull << (c->n - nq))));
         CUDA_TRY(c, qk::launch_measure_collapse((int)c->prec, c->d_state, c->n, ma, c->d_slots, c->sms, c->stream));
     }
+    if (outcome && c->capturing) return fail(c, QK_ESTATE, "measure with a host outcome is not allowed while capturing");
     if (outcome) {
         std::vector<qk::MeasSlot> h(nq);
         CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->d_slots, sizeof(qk::MeasSlot) * nq, cudaMemcpyDeviceToHost, c->stream));
@@ -867,6 +890,7 @@ qk_status qk_measure(qk_ctx *c, const int *qubits, int nq, const double *uniform
 
 qk_status qk_read_cbits(qk_ctx *c, uint8_t *out, int n) {
     if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "read_cbits");
     if (n < 0 || n > c->ncb || (n > 0 && !out)) return fail(c, QK_EINVAL, "read_cbits: bad count");
     qk_status s = flush(c);
     if (s != QK_OK) return s;
@@ -877,6 +901,7 @@ qk_status qk_read_cbits(qk_ctx *c, uint8_t *out, int n) {
 
 qk_status qk_write_cbits(qk_ctx *c, int first, const uint8_t *in, int n) {
     if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "write_cbits");
     if (first < 0 || n < 0 || first + n > c->ncb || (n > 0 && !in)) return fail(c, QK_EINVAL, "write_cbits: bad range");
     for (int a = 0; a < n; ++a)
         if (in[a] > 1) return fail(c, QK_EINVAL, "write_cbits: values must be 0 or 1");
@@ -891,6 +916,7 @@ qk_status qk_write_cbits(qk_ctx *c, int first, const uint8_t *in, int n) {
 
 qk_status qk_get_state(qk_ctx *c, void *host_out, size_t bytes) {
     if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "get_state");
     if (c->n == 0 || !host_out || bytes != c->state_bytes)
         return fail(c, QK_EINVAL, "get_state: need a buffer of exactly %zu bytes", c->state_bytes);
     qk_status s = flush(c);
@@ -903,6 +929,7 @@ qk_status qk_get_state(qk_ctx *c, void *host_out, size_t bytes) {
 
 qk_status qk_set_state(qk_ctx *c, const void *host_in, size_t bytes) {
     if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "set_state");
     if (c->n == 0 || !host_in || bytes != c->state_bytes)
         return fail(c, QK_EINVAL, "set_state: need a buffer of exactly %zu bytes", c->state_bytes);
     c->pending.clear();
@@ -924,6 +951,7 @@ qk_status qk_reset(qk_ctx *c) {
 
 qk_status qk_device_state(qk_ctx *c, void **dptr, size_t *bytes) {
     if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "device_state");
     if (!dptr || !bytes) return fail(c, QK_EINVAL, "device_state: null output");
     qk_status s = flush(c);
     if (s == QK_OK) s = canonicalize(c);
@@ -940,9 +968,80 @@ qk_status qk_flush(qk_ctx *c) {
 
 qk_status qk_sync(qk_ctx *c) {
     if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "sync");
     qk_status s = flush(c);
     if (s != QK_OK) return s;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return QK_OK;
+}
+
+qk_status qk_capture_begin(qk_ctx *c) {
+    if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "capture_begin");
+    if (c->n == 0) return fail(c, QK_ESTATE, "capture_begin: no qubits");
+    qk_status s = flush(c);
+    if (s == QK_OK) s = canonicalize(c);
+    if (s != QK_OK) return s;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    c->cap_state0 = c->d_state;
+    return QK_OK;
+}
+
+qk_status qk_capture_end(qk_ctx *c, qk_graph **out) {
+    if (!c) return QK_EINVAL;
+    if (!c->capturing) return fail(c, QK_ESTATE, "capture_end without capture_begin");
+    if (!out) return fail(c, QK_EINVAL, "capture_end: null output");
+    *out = nullptr;
+    qk_status s = flush(c);
+    if (s == QK_OK) s = canonicalize(c);        // back to the identity qubit map
+    if (s == QK_OK && c->d_state != c->cap_state0) {
+        // an odd number of out-of-place passes: copy back so that replays compose
+        if (cudaMemcpyAsync(c->cap_state0, c->d_state, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream) !=
+            cudaSuccess)
+            s = fail(c, QK_ECUDA, "capture_end: copy-back failed");
+        std::swap(c->d_state, c->d_scratch);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    c->capturing = false;
+    if (s != QK_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return fail(c, QK_ECUDA, "cudaStreamEndCapture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+    if (e2 != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(c, QK_ECUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e2));
+    }
+    qk_graph *g = new (std::nothrow) qk_graph{c, graph, exec};
+    if (!g) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(c, QK_ENOMEM, "capture_end: out of host memory");
+    }
+    *out = g;
+    return QK_OK;
+}
+
+qk_status qk_graph_launch(qk_graph *g) {
+    if (!g) return QK_EINVAL;
+    qk_ctx *c = g->ctx;
+    NOT_WHILE_CAPTURING(c, "graph_launch");
+    qk_status s = flush(c);
+    if (s == QK_OK) s = canonicalize(c);   // the graph expects the identity map
+    if (s != QK_OK) return s;
+    CUDA_TRY(c, cudaGraphLaunch(g->exec, c->stream));
+    return QK_OK;
+}
+
+qk_status qk_graph_destroy(qk_graph *g) {
+    if (!g) return QK_EINVAL;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
     return QK_OK;
 }
 

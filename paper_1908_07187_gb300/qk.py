@@ -74,6 +74,10 @@ _SIGS = {
     "qk_get_counters": ([_P, _U64P, _U64P, _U64P], ctypes.c_int),
     "qk_reset_counters": ([_P], ctypes.c_int),
     "qk_profile": ([_P, _U64P, _DP, _DP], ctypes.c_int),
+    "qk_capture_begin": ([_P], ctypes.c_int),
+    "qk_capture_end": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
+    "qk_graph_launch": ([_P], ctypes.c_int),
+    "qk_graph_destroy": ([_P], ctypes.c_int),
     "qk_last_error": ([_P], ctypes.c_char_p),
     "qk_status_str": ([ctypes.c_int], ctypes.c_char_p),
 }
@@ -269,6 +273,14 @@ class Context:
     def sync(self):
         self._check(_lib.qk_sync(self._h))
 
+    def capture_begin(self):
+        self._check(_lib.qk_capture_begin(self._h))
+
+    def capture_end(self) -> "Graph":
+        g = _P()
+        self._check(_lib.qk_capture_end(self._h, ctypes.byref(g)))
+        return Graph(self, g)
+
     def counters(self) -> Dict[str, int]:
         a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         self._check(_lib.qk_get_counters(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
@@ -284,6 +296,28 @@ class Context:
         self._check(_lib.qk_profile(self._h, L, M, B))
         return {LAUNCH_CLASSES[k]: {"launches": int(L[k]), "ms": M[k], "bytes": B[k]}
                 for k in range(NUM_LAUNCH_CLASSES)}
+
+
+class Graph:
+    """A captured CUDA graph of libqk calls on one context (qk_capture_end)."""
+
+    def __init__(self, ctx: Context, handle):
+        self._ctx = ctx
+        self._g = handle
+
+    def launch(self):
+        self._ctx._check(_lib.qk_graph_launch(self._g))
+
+    def close(self):
+        if getattr(self, "_g", None):
+            _lib.qk_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def run_ops(ctx: Context, ops) -> None:

@@ -400,3 +400,57 @@ def test_fused_kitaev_stage_rejects_bad_arguments(qk):
     with pytest.raises(qk.QKError):
         ctx.apply_kitaev_stage(0, gid, [1, 2, 3, 4], [], 1.0, 0)      # uniform outside [0, 1)
     ctx.close()
+
+
+# -- CUDA graph capture ------------------------------------------------------------------------
+
+def test_graph_replay_of_a_kitaev_run_matches_direct_run(qk):
+    N, a = workloads.kitaev_parameters(8, seed=3)
+    circ = workloads.kitaev_circuit(N, a, seed=9)
+    ref = oracle.run_circuit(circ)
+    ctx = qk.Context("c64", "fused")
+    ctx.add_qubits(circ.n_qubits)
+    ctx.add_cbits(circ.n_cbits)
+    qk.run_kitaev_fused(ctx, circ)          # defines the gates, allocates the gather buffer
+    ctx.sync()
+    ctx.capture_begin()
+    with pytest.raises(qk.QKError) as e:
+        ctx.read_cbits()
+    assert e.value.status == qk.QK_ESTATE
+    ctx.reset()
+    qk.run_kitaev_fused(ctx, circ)
+    g = ctx.capture_end()
+    for _ in range(3):
+        ctx.write_cbits(0, [0] * circ.n_cbits)
+        g.launch()
+        assert list(ctx.read_cbits()) == [int(x) for x in ref.cbits]
+        check_state(ctx.get_state(), ref.psi, "c64")
+    g.close()
+    ctx.close()
+
+
+def test_graph_replays_compose_with_relabels_and_odd_gathers(qk):
+    n = 14
+    psi = workloads.random_state(n, 5)
+    ctx = new_ctx(qk, n, "c64", "fused", psi)
+    gid = ctx.define_gate_perm_mulmod(5, 7, 29)
+    ctx.apply_gate(gid, [9, 3, 12, 0, 6], [1])   # allocates the gather buffer once
+    ref = oracle.OracleState(n, psi=psi)
+    ref.apply_mulmod(7, 29, [9, 3, 12, 0, 6], [1])
+    ctx.capture_begin()
+    ctx.apply_gate("h", [0])
+    ctx.apply_gate("swap", [0, 11])
+    ctx.apply_gate("u3", [11], params=[0.4, 1.0, 2.0])
+    ctx.apply_gate(gid, [9, 3, 12, 0, 6], [1])   # one out-of-place gather: odd
+    ctx.apply_gate("p", [4], controls=[13], params=[0.9])
+    g = ctx.capture_end()
+    for _ in range(2):
+        g.launch()
+        ref.apply_matrix(oracle.GATES_1Q["h"], [0])
+        ref.apply_matrix(oracle.SWAP, [0, 11])
+        ref.apply_matrix(oracle.u3(0.4, 1.0, 2.0), [11])
+        ref.apply_mulmod(7, 29, [9, 3, 12, 0, 6], [1])
+        ref.apply_matrix(oracle.phase(0.9), [4], [13])
+    check_state(ctx.get_state(), ref.psi, "c64")
+    g.close()
+    ctx.close()

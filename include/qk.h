@@ -72,7 +72,8 @@ typedef struct {
     int max_pending;          /* queued ops that force a flush; 0 = default (4096)   */
     int profile;              /* 1: time every launch with CUDA events (qk_profile)  */
     size_t hbm_budget_bytes;  /* 0 = no limit beyond free device memory             */
-    int reserved[8];          /* must be zero                                         */
+    int no_tensor_cores;      /* 1: dense 5-qubit blocks on CUDA cores only           */
+    int reserved[7];          /* must be zero                                         */
 } qk_options;
 
 /* Built-in gate ids for qk_apply_gate (negative; user gates get ids >= 0).
@@ -120,7 +121,11 @@ qk_status qk_add_cbits(qk_ctx *ctx, int n, int *first_cbit_out);
 /* Define a gate "as a matrix" (Q-Kit section, command 4): k qubits (1..6), u is the
  * 2^k x 2^k matrix, row-major, interleaved (re, im) doubles, copied.  The matrix
  * must satisfy max |U^dagger U - I| <= unitarity_tol (QK_ENOTUNITARY otherwise).
- * *gate_id receives an id >= 0 valid for the life of the context. */
+ * *gate_id receives an id >= 0 valid for the life of the context.  A 5-qubit
+ * complex64 gate without controls whose targets are the five lowest physical
+ * qubits runs on the tensor cores (3xTF32 batched complex GEMM); other dense
+ * gates run on CUDA cores.  qk_sync reports QK_ETIMEOUT if a tensor-core pass
+ * hit its bounded wait. */
 qk_status qk_define_gate_matrix(qk_ctx *ctx, int k, const double *u, double unitarity_tol, int *gate_id);
 
 /* Define a gate "as a function" (Q-Kit section, command 4; QuModExpUaj of

@@ -1,0 +1,278 @@
+// K4, tensor-core form: a dense 5-qubit complex64 unitary U on the five lowest
+// physical qubits, applied as a batched complex matrix product on tcgen05.
+//
+// The state is a matrix of 2^(n-5) group rows; a row holds the 32 amplitudes
+// that share the upper bits, stored as 64 interleaved floats (re, im).  With the
+// real 64 x 64 embedding B of U (B[2x][2r] = Re U[r][x], B[2x+1][2r] = -Im U,
+// B[2x][2r+1] = Im U, B[2x+1][2r+1] = Re U) every row becomes Y = X B, i.e. a
+// GEMM with M = 2^(n-5), N = K = 64.  TF32 tensor cores keep 10 mantissa bits,
+// so the product uses the 3xTF32 split X = Xh + Xl, B = Bh + Bl (Xh, Bh the
+// inputs with the low 13 mantissa bits cleared) and D = Xh Bh + Xh Bl + Xl Bh in
+// FP32, close to full FP32 accuracy (Markidis et al., "NVIDIA Tensor Core
+// programmability, performance & precision", 2018).
+//
+// Per CTA (128 threads): a 128-row tile of X arrives by TMA (128-byte swizzle)
+// into shared memory; the threads write Xl beside it; one thread issues 24
+// tcgen05.mma (3 products x 8 K-steps of 8) into a 128 x 64 FP32 accumulator in
+// tensor memory; the four warps read their 32 rows back with tcgen05.ld and
+// store them in place.  Every mbarrier wait has an iteration limit; on timeout
+// the kernel records an error and leaves the loop, releasing its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qk_kernels.cuh"
+
+namespace qk {
+namespace {
+
+constexpr int kRows = 128;                    // rows per tile = MMA M
+constexpr int kCols = 64;                     // floats per row = MMA K = MMA N
+constexpr int kChunk = kRows * 128;           // one 128-byte-wide K chunk of the tile (16 KiB)
+constexpr int kTile = 2 * kChunk;             // 32 KiB
+constexpr int kBChunk = kCols * 128;          // 8 KiB
+constexpr int kB = 2 * kBChunk;               // 16 KiB
+constexpr int kThreads = 128;
+constexpr int kSmemBytes = 1024 + 2 * kTile + 2 * kB + 64;
+constexpr uint32_t kWaitLimit = 1u << 22;     // bounded mbarrier waits
+constexpr uint32_t kTmemCols = 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait on an mbarrier phase; false after kWaitLimit tries
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 32) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (stride byte offset), leading byte offset unused.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                 // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 64
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (row, col) in a K-major, 128-byte-swizzled tile with
+// `rows` rows (two 128-byte K chunks of rows x 128 bytes)
+__device__ __forceinline__ uint32_t swz_offset(int row, int col, int rows) {
+    const int chunk = col >> 5, c = col & 31;
+    return (uint32_t)(chunk * rows * 128 + row * 128 + ((((c >> 2) ^ (row & 7)) << 4) | ((c & 3) << 2)));
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+    k_block_tc(float *__restrict__ psi, const __grid_constant__ CUtensorMap tmap, const float *__restrict__ bh_g,
+               const float *__restrict__ bl_g, uint64_t n_groups, uint64_t n_tiles, int *err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = smem;                  // X tile as loaded (Xh: the MMA ignores the low bits)
+    unsigned char *sAl = smem + kTile;         // Xl
+    unsigned char *sBh = smem + 2 * kTile;
+    unsigned char *sBl = sBh + kB;
+    uint64_t *bars = (uint64_t *)(sBl + kB);   // [0] tile loaded, [1] MMAs done
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar_full = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+
+    if (tid == 0) {
+        mbar_init(bar_full, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // Bh, Bl: 64 x 64 row-major (row = output column n, col = k) into the swizzled layout
+    for (int e = tid; e < kCols * kCols; e += kThreads) {
+        const int n = e >> 6, k = e & 63;
+        *(float *)(sBh + swz_offset(n, k, kCols)) = bh_g[e];
+        *(float *)(sBl + swz_offset(n, k, kCols)) = bl_g[e];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    bool ok = true;
+    uint32_t phase = 0;
+    for (uint64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, phase ^= 1u) {
+        if (tid == 0) {
+            mbar_expect_tx(bar_full, kTile);
+            tma_load_2d(smem_u32(sA), &tmap, 0, (int)(tile * kRows), bar_full);
+            tma_load_2d(smem_u32(sA + kChunk), &tmap, 32, (int)(tile * kRows), bar_full);
+        }
+        // every thread takes the same decision, so the barriers below stay matched
+        if (!__syncthreads_and(mbar_wait(bar_full, phase))) {
+            ok = false;
+            break;
+        }
+        // Xl = X - Xh, elementwise over the whole tile (same swizzled positions)
+        {
+            const float4 *src = (const float4 *)sA;
+            float4 *dst = (float4 *)sAl;
+#pragma unroll 4
+            for (int e = tid; e < kTile / 16; e += kThreads) {
+                const float4 x = src[e];
+                float4 l;
+                l.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u);
+                l.y = x.y - __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u);
+                l.z = x.z - __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u);
+                l.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u);
+                dst[e] = l;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned char *As[3] = {sA, sA, sAl};
+            const unsigned char *Bs[3] = {sBh, sBl, sBh};
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    const uint32_t koff = (uint32_t)((kk & 3) * 32);
+                    const uint64_t a = smem_desc(smem_u32(As[p] + (kk >> 2) * kChunk) + koff);
+                    const uint64_t b = smem_desc(smem_u32(Bs[p] + (kk >> 2) * kBChunk) + koff);
+                    mma_tf32(tmem, a, b, (p | kk) ? 1u : 0u);
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
+                         : "memory");
+        }
+        if (!__syncthreads_and(mbar_wait(bar_mma, phase))) {
+            ok = false;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: warp w holds rows 32w..32w+31 (TMEM lanes), 64 FP32 columns
+        {
+            float v0[32], v1[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            tmem_ld32(taddr, v0);
+            tmem_ld32(taddr + 32, v1);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const uint64_t row = tile * kRows + (uint64_t)(warp * 32 + lane);
+            if (row < n_groups) {
+                float4 *dst = (float4 *)(psi + row * kCols);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dst[q] = make_float4(v0[4 * q], v0[4 * q + 1], v0[4 * q + 2], v0[4 * q + 3]);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    dst[8 + q] = make_float4(v1[4 * q], v1[4 * q + 1], v1[4 * q + 2], v1[4 * q + 3]);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+}  // namespace
+
+cudaError_t launch_block_tc(void *psi, int n, const float *bh, const float *bl, int *err, int sms, cudaStream_t s) {
+    if (n < 5) return cudaErrorInvalidValue;
+    if (((uintptr_t)psi & 15) != 0) return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const uint64_t n_groups = 1ull << (n - 5);
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {64, (cuuint64_t)n_groups};
+    const cuuint64_t strides[1] = {256};          // bytes between group rows
+    const cuuint32_t box[2] = {32, (cuuint32_t)kRows};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, psi, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
+    uint64_t grid = n_tiles < (uint64_t)(2 * sms) ? n_tiles : (uint64_t)(2 * sms);
+    k_block_tc<<<(unsigned)grid, kThreads, kSmemBytes, s>>>((float *)psi, map, bh, bl, n_groups, n_tiles, err);
+    return cudaGetLastError();
+}
+
+}  // namespace qk

@@ -30,6 +30,8 @@ struct GateDef {
     void *d_mat = nullptr;        // working-precision copy on the device
     uint64_t c = 0, N = 0, cinv = 0;
     uint32_t *d_finv = nullptr;
+    // 5-qubit gates on the tensor cores: split real embeddings per target order
+    std::vector<std::pair<uint32_t, float *>> tc_cache;
 };
 
 struct ProfRec {
@@ -60,6 +62,7 @@ struct qk_ctx {
     uint8_t *d_cbits = nullptr;
 
     double *d_partials = nullptr;
+    int *d_err = nullptr;          // set by a kernel whose bounded wait gave up
     int meas_blocks = 0;
     qk::MeasSlot *d_slots = nullptr;
     int slot_cap = 0;
@@ -381,6 +384,51 @@ qk_status ensure_slots(qk_ctx *c, int nq) {
     return QK_OK;
 }
 
+// Dense 5-qubit gate on physical qubits 0..4 via the tensor-core kernel.  The
+// real embedding of U, with rows and columns permuted to the physical order of
+// the targets, is split into TF32 high and low parts once per target order.
+qk_status apply_block_tc(qk_ctx *c, int gate_id, const int *targets, uint32_t key) {
+    GateDef &g = c->gates[gate_id];
+    float *dev = nullptr;
+    for (auto &e : g.tc_cache)
+        if (e.first == key) dev = e.second;
+    if (!dev) {
+        if (c->capturing) return fail(c, QK_ESTATE, "tensor-core matrices would be allocated during capture");
+        int pa[5];
+        for (int a = 0; a < 5; ++a) pa[a] = c->l2p[targets[a]];
+        auto value = [&](int x) {  // gate register value of physical low-bit index x
+            int v = 0;
+            for (int a = 0; a < 5; ++a) v |= ((x >> pa[a]) & 1) << (4 - a);
+            return v;
+        };
+        std::vector<float> bh(64 * 64), bl(64 * 64);
+        for (int r = 0; r < 32; ++r)
+            for (int x = 0; x < 32; ++x) {
+                const cd u = g.m[(size_t)value(r) * 32 + value(x)];
+                const float re = (float)u.real(), im = (float)u.imag();
+                const float vals[4] = {re, -im, im, re};          // (2r,2x) (2r,2x+1) (2r+1,2x) (2r+1,2x+1)
+                const int idx[4] = {(2 * r) * 64 + 2 * x, (2 * r) * 64 + 2 * x + 1, (2 * r + 1) * 64 + 2 * x,
+                                    (2 * r + 1) * 64 + 2 * x + 1};
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t bits;
+                    std::memcpy(&bits, &vals[q], 4);
+                    bits &= 0xFFFFE000u;
+                    float hi;
+                    std::memcpy(&hi, &bits, 4);
+                    bh[idx[q]] = hi;
+                    bl[idx[q]] = vals[q] - hi;
+                }
+            }
+        CUDA_TRY(c, cudaMalloc(&dev, sizeof(float) * 2 * 64 * 64));
+        CUDA_TRY(c, cudaMemcpy(dev, bh.data(), sizeof(float) * 64 * 64, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(dev + 64 * 64, bl.data(), sizeof(float) * 64 * 64, cudaMemcpyHostToDevice));
+        g.tc_cache.push_back({key, dev});
+    }
+    LaunchScope ls(c, 3, (double)full_pass_bytes(c));
+    CUDA_TRY(c, qk::launch_block_tc(c->d_state, c->n, dev, dev + 64 * 64, c->d_err, c->sms, c->stream));
+    return QK_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -453,7 +501,9 @@ qk_status qk_create(qk_ctx **out, qk_precision precision, void *cuda_stream, con
         c->own_stream = true;
     }
     c->meas_blocks = c->sms * kMeasBlocksPerSM;
-    if (cudaMalloc(&c->d_partials, sizeof(double) * 2 * c->meas_blocks) != cudaSuccess) {
+    if (cudaMalloc(&c->d_partials, sizeof(double) * 2 * c->meas_blocks) != cudaSuccess ||
+        cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
         qk_destroy(c);
         return QK_ENOMEM;
     }
@@ -472,7 +522,9 @@ qk_status qk_destroy(qk_ctx *c) {
     for (auto &g : c->gates) {
         if (g.d_mat) cudaFree(g.d_mat);
         if (g.d_finv) cudaFree(g.d_finv);
+        for (auto &e : g.tc_cache) cudaFree(e.second);
     }
+    if (c->d_err) cudaFree(c->d_err);
     if (c->d_swap_mat) cudaFree(c->d_swap_mat);
     if (c->d_state) cudaFree(c->d_state);
     if (c->d_scratch) cudaFree(c->d_scratch);
@@ -713,6 +765,14 @@ qk_status qk_apply_gate(qk_ctx *c, int gate_id, const int *targets, int nt, cons
         }
         qk_status s = flush(c);
         if (s != QK_OK) return s;
+        if (g.k == 5 && c->prec == QK_C64 && nc == 0 && ncc == 0 && !c->opt.no_tensor_cores) {
+            uint32_t phys = 0, key = 0;
+            for (int a = 0; a < 5; ++a) {
+                phys |= 1u << c->l2p[targets[a]];
+                key |= (uint32_t)c->l2p[targets[a]] << (3 * a);
+            }
+            if (phys == 0x1Fu) return apply_block_tc(c, gate_id, targets, key);
+        }
         qk::MatKArgs a{};
         a.k = g.k;
         std::vector<int> pos;
@@ -972,6 +1032,12 @@ qk_status qk_sync(qk_ctx *c) {
     qk_status s = flush(c);
     if (s != QK_OK) return s;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int err = 0;
+    CUDA_TRY(c, cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
+        return fail(c, QK_ETIMEOUT, "a tensor-core pass gave up a bounded wait; the state is not valid");
+    }
     return QK_OK;
 }
 

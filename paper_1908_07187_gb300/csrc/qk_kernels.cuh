@@ -206,6 +206,10 @@ cudaError_t launch_kitaev_reduce(int prec, const void *psi, const KitaevArgs &a,
                                  double *partials, int nblocks, cudaStream_t s);
 cudaError_t launch_kitaev_update(int prec, const void *psi, void *out, const KitaevArgs &a, const uint8_t *cbits,
                                  const MeasSlot *slot, int sms, cudaStream_t s);
+// K4 on tensor cores (kernels_block_tc.cu): dense 5-qubit complex64 unitary on
+// physical qubits 0..4; bh/bl are the 64 x 64 split real embedding (row = output
+// column); err receives 1 if a bounded wait gave up.
+cudaError_t launch_block_tc(void *psi, int n, const float *bh, const float *bl, int *err, int sms, cudaStream_t s);
 cudaError_t launch_set_basis(int prec, void *psi, uint64_t index, cudaStream_t s);
 cudaError_t launch_relabel(int prec, const void *in, void *out, const RelabelArgs &a, int sms,
                            cudaStream_t s);

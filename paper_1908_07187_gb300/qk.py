@@ -36,7 +36,7 @@ GATE = {
 class Options(ctypes.Structure):
     _fields_ = [("exec_mode", ctypes.c_int), ("tile_qubits", ctypes.c_int), ("max_pending", ctypes.c_int),
                 ("profile", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
-                ("reserved", ctypes.c_int * 8)]
+                ("no_tensor_cores", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 _P = ctypes.c_void_p
@@ -107,7 +107,8 @@ class Context:
     """One libqk context: a state vector on the current CUDA device."""
 
     def __init__(self, precision: str = "c64", exec_mode: str = "fused", stream: Optional[int] = None,
-                 tile_qubits: int = 0, profile: bool = False, hbm_budget_bytes: int = 0, max_pending: int = 0):
+                 tile_qubits: int = 0, profile: bool = False, hbm_budget_bytes: int = 0, max_pending: int = 0,
+                 tensor_cores: bool = True):
         opt = Options()
         opt.exec_mode = QK_EXEC_FUSED if exec_mode == "fused" else QK_EXEC_PLAIN
         if exec_mode not in ("fused", "plain"):
@@ -116,6 +117,7 @@ class Context:
         opt.max_pending = max_pending
         opt.profile = 1 if profile else 0
         opt.hbm_budget_bytes = hbm_budget_bytes
+        opt.no_tensor_cores = 0 if tensor_cores else 1
         self.precision = precision
         self.cdtype = np.complex64 if precision == "c64" else np.complex128
         prec = QK_C64 if precision == "c64" else QK_C128

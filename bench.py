@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-pass-per-gate comparison")
     ap.add_argument("--no-kitaev", action="store_true", help="skip the Kitaev order-finding measurement")
+    ap.add_argument("--no-block", action="store_true", help="skip the dense 5-qubit block measurement")
     return ap.parse_args()
 
 
@@ -245,6 +246,42 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+# ---------------------------------------------------------------------------
+# dense 5-qubit block (secondary measurement)
+# ---------------------------------------------------------------------------
+def block_measurement(qk, torch, stream, n: int, reps: int = 10):
+    """One dense 5-qubit unitary on qubits 0..4 of an n-qubit complex64 state,
+    tensor cores (3xTF32) vs CUDA cores; device time per pass with CUDA events."""
+    import numpy as np
+
+    g = np.random.Generator(np.random.PCG64(5))
+    z = (g.standard_normal((32, 32)) + 1j * g.standard_normal((32, 32))) / np.sqrt(2)
+    q, r = np.linalg.qr(z)
+    U = q * (np.diag(r) / np.abs(np.diag(r)))
+    out = {"n": n, "alg_bytes_per_pass": 2 * 8 * 2 ** n,
+           "alg_flops_per_pass": 2 ** (n - 5) * 64 * 64 * 2}
+    for tc in (True, False):
+        ctx = qk.Context("c64", "plain", stream=stream.cuda_stream, tensor_cores=tc)
+        ctx.add_qubits(n)
+        gid = ctx.define_gate_matrix(U)
+        ctx.apply_gate("h", [0])
+        for _ in range(2):
+            ctx.apply_gate(gid, [4, 3, 2, 1, 0])
+        ctx.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.apply_gate(gid, [4, 3, 2, 1, 0])
+        e1.record(stream)
+        ctx.sync()
+        ms = e0.elapsed_time(e1) / reps
+        key = "tensor_core" if tc else "cuda_core"
+        out[key] = {"ms_per_pass": round(ms, 4), "GBps": round(out["alg_bytes_per_pass"] / ms / 1e6, 1),
+                    "TFLOPs": round(out["alg_flops_per_pass"] / ms / 1e9, 2)}
+        ctx.close()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -449,6 +486,9 @@ def main():
     kitaev = None
     if not args.no_kitaev:
         kitaev = kitaev_measurement(qk, torch, stream)
+    block = None
+    if not args.no_block:
+        block = block_measurement(qk, torch, stream, n)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -470,6 +510,7 @@ def main():
             "cpu_baseline": cpu,
             "plain_path": plain,
             "kitaev": kitaev,
+            "block5": block,
             "launch_profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items() if v["launches"]},
             "clocks": clk,
         }

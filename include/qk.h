@@ -257,6 +257,39 @@ qk_status qk_capture_end(qk_ctx *ctx, qk_graph **out);
 qk_status qk_graph_launch(qk_graph *g);
 qk_status qk_graph_destroy(qk_graph *g);
 
+/* Batched small circuits (no counterpart in the paper; it serves many small
+ * requests with one launch).  A batch holds up to thousands of independent
+ * circuits of 1..13 qubits (complex64, up to 64 cbits each); each runs entirely
+ * in one CTA's shared memory, from |0...0> and cbits 0, with the same op
+ * semantics as a context: built-in 1-target gates with quantum controls and
+ * classical conditions (qk_batch_apply_gate), the controlled mul-mod oracle of
+ * Appendix A (qk_batch_apply_mulmod, register <= 16 qubits), and sequential
+ * single-qubit measurement into cbits (qk_batch_measure).  qk_batch_run uploads
+ * the programs and launches (one launch per distinct qubit count) on the batch's
+ * stream without waiting; qk_batch_done polls; qk_batch_read waits and copies a
+ * circuit's cbits and (if stored) final state.  Add ops to the most recently
+ * added circuit.  qk_batch_clear waits for a previous run and empties the batch.
+ * Errors: QK_EINVAL (sizes, qubit lists, params), QK_ENOTBIJECTIVE, QK_ESTATE
+ * (op before any circuit), QK_ENOMEM, QK_ECUDA; message in qk_batch_last_error. */
+typedef struct qk_batch qk_batch;
+qk_status qk_batch_create(qk_batch **out, void *cuda_stream);
+qk_status qk_batch_destroy(qk_batch *b);
+qk_status qk_batch_clear(qk_batch *b);
+qk_status qk_batch_add_circuit(qk_batch *b, int n, int ncbits, int *index);
+qk_status qk_batch_apply_gate(qk_batch *b, int gate_id, const int *targets, int nt, const int *controls, int nc,
+                              const int *cond_cbits, int ncc, const double *params, int np);
+qk_status qk_batch_apply_mulmod(qk_batch *b, const int *targets, int w, const int *controls, int nc, uint64_t c,
+                                uint64_t N);
+qk_status qk_batch_measure(qk_batch *b, const int *qubits, int nq, const double *uniforms, const int *dest_cbits);
+qk_status qk_batch_run(qk_batch *b, int store_states);
+/* 1 when the last run has finished, 0 while it runs, -1 on error. */
+int qk_batch_done(qk_batch *b);
+qk_status qk_batch_read(qk_batch *b, int circuit, uint8_t *cbits, int ncb, void *state, size_t bytes);
+/* All circuits' cbits, concatenated in circuit order (sum of their cbit counts). */
+qk_status qk_batch_read_all_cbits(qk_batch *b, uint8_t *out, size_t n);
+int qk_batch_num_circuits(const qk_batch *b);
+const char *qk_batch_last_error(const qk_batch *b);
+
 /* Counters since creation or the last reset_counters: kernel launches, passes
  * over the state (launches that stream the full state), and algorithmic bytes
  * (2^n * amplitude size * 2 per full pass, read + write). */

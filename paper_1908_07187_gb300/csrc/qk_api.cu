@@ -16,6 +16,7 @@
 
 #include "qk.h"
 #include "qk_kernels.cuh"
+#include "qk_host.h"
 #include "qk_plan.h"
 
 using cd = std::complex<double>;
@@ -198,44 +199,6 @@ qk_status upload_matrix(qk_ctx *c, const std::vector<cd> &m, void **dptr) {
     CUDA_TRY(c, cudaMalloc(dptr, host.size()));
     CUDA_TRY(c, cudaMemcpy(*dptr, host.data(), host.size(), cudaMemcpyHostToDevice));
     return QK_OK;
-}
-
-// ---------------------------------------------------------------------------
-// built-in gate matrices (textbook definitions; FP64)
-// ---------------------------------------------------------------------------
-bool builtin_matrix(int id, const double *p, int np, cd m[4], int &ntargets) {
-    const double r2 = 1.0 / std::sqrt(2.0);
-    const cd I(0, 1);
-    ntargets = 1;
-    switch (id) {
-        case QK_GATE_X: m[0] = 0; m[1] = 1; m[2] = 1; m[3] = 0; return np == 0;
-        case QK_GATE_Y: m[0] = 0; m[1] = -I; m[2] = I; m[3] = 0; return np == 0;
-        case QK_GATE_Z: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = -1; return np == 0;
-        case QK_GATE_H: m[0] = r2; m[1] = r2; m[2] = r2; m[3] = -r2; return np == 0;
-        case QK_GATE_S: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = I; return np == 0;
-        case QK_GATE_SDG: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = -I; return np == 0;
-        case QK_GATE_T: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = std::polar(1.0, M_PI / 4); return np == 0;
-        case QK_GATE_TDG: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = std::polar(1.0, -M_PI / 4); return np == 0;
-        case QK_GATE_U3: {
-            if (np != 3 || !p) return false;
-            const double c = std::cos(p[0] / 2), s = std::sin(p[0] / 2);
-            m[0] = c;
-            m[1] = -std::polar(1.0, p[2]) * s;
-            m[2] = std::polar(1.0, p[1]) * s;
-            m[3] = std::polar(1.0, p[1] + p[2]) * c;
-            return true;
-        }
-        case QK_GATE_P:
-            if (np != 1 || !p) return false;
-            m[0] = 1; m[1] = 0; m[2] = 0; m[3] = std::polar(1.0, p[0]);
-            return true;
-        case QK_GATE_RZ:
-            if (np != 1 || !p) return false;
-            m[0] = std::polar(1.0, -p[0] / 2); m[1] = 0; m[2] = 0; m[3] = std::polar(1.0, p[0] / 2);
-            return true;
-        case QK_GATE_SWAP: ntargets = 2; return np == 0;
-        default: return false;
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -627,19 +590,6 @@ qk_status qk_define_gate_matrix(qk_ctx *c, int k, const double *u, double tol, i
     return QK_OK;
 }
 
-static uint64_t modinv(uint64_t a, uint64_t N, bool &ok) {
-    // extended Euclid on signed 128-bit
-    __int128 t = 0, nt = 1, r = (__int128)N, nr = (__int128)(a % N);
-    while (nr != 0) {
-        __int128 q = r / nr, tmp;
-        tmp = t - q * nt; t = nt; nt = tmp;
-        tmp = r - q * nr; r = nr; nr = tmp;
-    }
-    ok = (r == 1);
-    if (t < 0) t += N;
-    return (uint64_t)t;
-}
-
 qk_status qk_define_gate_perm_mulmod(qk_ctx *c, int w, uint64_t cc, uint64_t N, int *gate_id) {
     if (!c) return QK_EINVAL;
     NOT_WHILE_CAPTURING(c, "define_gate_perm_mulmod");
@@ -647,7 +597,7 @@ qk_status qk_define_gate_perm_mulmod(qk_ctx *c, int w, uint64_t cc, uint64_t N, 
         return fail(c, QK_EINVAL, "define_gate_perm_mulmod: bad w=%d or N=%llu", w, (unsigned long long)N);
     if (cc >= N) return fail(c, QK_EINVAL, "define_gate_perm_mulmod: c must be < N");
     bool ok = false;
-    uint64_t inv = modinv(cc, N, ok);
+    uint64_t inv = qk::modinv(cc, N, ok);
     if (!ok) return fail(c, QK_ENOTBIJECTIVE, "x -> %llu x mod %llu is not a permutation (gcd != 1)",
                          (unsigned long long)cc, (unsigned long long)N);
     GateDef g;
@@ -701,7 +651,7 @@ qk_status qk_apply_gate(qk_ctx *c, int gate_id, const int *targets, int nt, cons
     if (gate_id < 0) {
         cd m[4];
         int ntg = 0;
-        if (!builtin_matrix(gate_id, params, np, m, ntg)) return fail(c, QK_EINVAL, "apply_gate: unknown built-in %d or bad params", gate_id);
+        if (!qk::builtin_matrix(gate_id, params, np, m, ntg)) return fail(c, QK_EINVAL, "apply_gate: unknown built-in %d or bad params", gate_id);
         if (nt != ntg) return fail(c, QK_EINVAL, "apply_gate: built-in %d takes %d targets", gate_id, ntg);
         if (gate_id == QK_GATE_SWAP) {
             if (nc == 0 && ncc == 0) {

@@ -1,0 +1,527 @@
+// K8: many small circuits in one launch.
+//
+// A circuit of n <= 13 qubits fits in shared memory (2^13 complex64 = 64 KiB),
+// so one CTA can run the whole circuit -- 2x2 gates with quantum controls,
+// diagonal gates, the controlled mul-mod oracle, mid-circuit measurements and
+// classically conditioned gates -- without touching HBM between gates.  A batch
+// launch gives every circuit its own CTA; the circuits are independent and may
+// differ in size and gate list.  This is the shared launch that serving uses for
+// small requests (one launch per batch instead of one launch per gate).
+//
+// Semantics match the per-gate engine op for op: measurement is one qubit at a
+// time in list order, P0 summed in FP64 over the (renormalised) state, outcome
+// 1 iff u >= P0, collapse and renormalise; cbits start at 0.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qk.h"
+#include "qk_host.h"
+
+namespace qk {
+namespace {
+
+constexpr int kBThreads = 256;
+constexpr int kBMaxQubits = 13;
+constexpr int kBMaxCbits = 64;
+
+enum BOpKind : uint8_t { B_U2 = 0, B_PHASE = 1, B_MULMOD = 2, B_MEASURE = 3 };
+
+// One op of a small-circuit program (64 bytes).
+struct BOp {
+    uint8_t kind, q, ncond, w;
+    uint8_t cond[4];
+    uint32_t cmask, val;       // controls (U2, MULMOD) / phase mask and value
+    union {
+        float m[8];            // U2: m00, m01, m10, m11 (re, im)
+        struct {
+            float re, im;      // PHASE factor
+        } ph;
+        struct {
+            uint32_t N, cinv;  // MULMOD: y -> cinv*y mod N gives the source register value
+            uint8_t rpos[16];  // register qubits, rpos[0] = MSB
+        } mm;
+        struct {
+            double u;          // MEASURE uniform
+            int32_t dest;      // destination cbit (-1: none)
+        } ms;
+    };
+    uint8_t pad[16];
+};
+static_assert(sizeof(BOp) == 64, "BOp layout");
+
+struct BCirc {
+    uint32_t op_begin, op_end;
+    uint32_t n, ncb;
+    uint32_t cb_off;
+    uint32_t pad;
+    uint64_t state_off;        // in amplitudes
+};
+
+__device__ __forceinline__ uint32_t ins0(uint32_t j, int pos) {
+    const uint32_t lo = j & ((1u << pos) - 1);
+    return ((j - lo) << 1) | lo;
+}
+
+__global__ void __launch_bounds__(kBThreads) k_batch(const BCirc *__restrict__ circs, const BOp *__restrict__ ops,
+                                                     float2 *__restrict__ states, uint8_t *__restrict__ cbits_out,
+                                                     int store_state) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const BCirc c = circs[blockIdx.x];
+    const int n = (int)c.n;
+    const uint32_t dim = 1u << n;
+    __shared__ double red[2][kBThreads / 32];
+    __shared__ uint8_t cb[kBMaxCbits];
+    __shared__ int s_m;
+    __shared__ float s_scale;
+    float2 *A = reinterpret_cast<float2 *>(sm);
+    float2 *B = A + dim;
+    const int tid = threadIdx.x;
+    for (uint32_t i = tid; i < dim; i += kBThreads) A[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+    for (int k = tid; k < kBMaxCbits; k += kBThreads) cb[k] = 0;
+    __syncthreads();
+
+    for (uint32_t oi = c.op_begin; oi < c.op_end; ++oi) {
+        const BOp &op = ops[oi];
+        bool act = true;
+        for (int k = 0; k < op.ncond; ++k) act = act && cb[op.cond[k]] != 0;
+        if (op.kind == B_U2) {
+            if (act) {
+                const float2 m00 = make_float2(op.m[0], op.m[1]), m01 = make_float2(op.m[2], op.m[3]);
+                const float2 m10 = make_float2(op.m[4], op.m[5]), m11 = make_float2(op.m[6], op.m[7]);
+                for (uint32_t p = tid; p < (dim >> 1); p += kBThreads) {
+                    const uint32_t i0 = ins0(p, op.q), i1 = i0 | (1u << op.q);
+                    if ((i0 & op.cmask) != op.cmask) continue;
+                    const float2 a = A[i0], b = A[i1];
+                    A[i0] = make_float2(m00.x * a.x - m00.y * a.y + m01.x * b.x - m01.y * b.y,
+                                        m00.x * a.y + m00.y * a.x + m01.x * b.y + m01.y * b.x);
+                    A[i1] = make_float2(m10.x * a.x - m10.y * a.y + m11.x * b.x - m11.y * b.y,
+                                        m10.x * a.y + m10.y * a.x + m11.x * b.y + m11.y * b.x);
+                }
+            }
+        } else if (op.kind == B_PHASE) {
+            if (act) {
+                const float fr = op.ph.re, fi = op.ph.im;
+                for (uint32_t i = tid; i < dim; i += kBThreads)
+                    if ((i & op.cmask) == op.val) {
+                        const float2 a = A[i];
+                        A[i] = make_float2(a.x * fr - a.y * fi, a.x * fi + a.y * fr);
+                    }
+            }
+        } else if (op.kind == B_MULMOD) {
+            for (uint32_t i = tid; i < dim; i += kBThreads) {
+                uint32_t src = i;
+                if (act && (i & op.cmask) == op.cmask) {
+                    uint32_t y = 0;
+                    for (int b = 0; b < op.w; ++b) y = (y << 1) | ((i >> op.mm.rpos[b]) & 1u);
+                    if (y < op.mm.N) {
+                        const uint32_t x = (uint32_t)(((uint64_t)op.mm.cinv * y) % op.mm.N);
+                        for (int b = 0; b < op.w; ++b) {
+                            const uint32_t bit = (x >> (op.w - 1 - b)) & 1u;
+                            src = (src & ~(1u << op.mm.rpos[b])) | (bit << op.mm.rpos[b]);
+                        }
+                    }
+                }
+                B[i] = A[src];
+            }
+            __syncthreads();
+            float2 *t = A;
+            A = B;
+            B = t;
+        } else {  // B_MEASURE on qubit q
+            double d0 = 0.0, d1 = 0.0;
+            for (uint32_t i = tid; i < dim; i += kBThreads) {
+                const float2 a = A[i];
+                const double pa = (double)a.x * a.x + (double)a.y * a.y;
+                if ((i >> op.q) & 1u) d1 += pa; else d0 += pa;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+                d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+            }
+            if ((tid & 31) == 0) {
+                red[0][tid >> 5] = d0;
+                red[1][tid >> 5] = d1;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double s0 = 0.0, s1 = 0.0;
+                for (int w = 0; w < kBThreads / 32; ++w) {
+                    s0 += red[0][w];
+                    s1 += red[1][w];
+                }
+                const double tot = s0 + s1;
+                const double p0 = tot > 0.0 ? s0 / tot : 1.0;
+                const int m = (op.ms.u >= p0) ? 1 : 0;
+                const double pm = m ? s1 : s0;
+                s_m = m;
+                s_scale = (float)(pm > 0.0 ? 1.0 / sqrt(pm) : 0.0);
+                if (op.ms.dest >= 0) cb[op.ms.dest] = (uint8_t)m;
+            }
+            __syncthreads();
+            const int m = s_m;
+            const float sc = s_scale;
+            for (uint32_t i = tid; i < dim; i += kBThreads) {
+                const float k = ((int)((i >> op.q) & 1u) == m) ? sc : 0.f;
+                const float2 a = A[i];
+                A[i] = make_float2(a.x * k, a.y * k);
+            }
+        }
+        __syncthreads();
+    }
+    for (uint32_t k = tid; k < c.ncb; k += kBThreads) cbits_out[c.cb_off + k] = cb[k];
+    if (store_state)
+        for (uint32_t i = tid; i < dim; i += kBThreads) states[c.state_off + i] = A[i];
+}
+
+}  // namespace
+}  // namespace qk
+
+// ===========================================================================
+// host side
+// ===========================================================================
+struct qk_batch {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sms = 148;
+    std::vector<qk::BOp> ops;
+    std::vector<qk::BCirc> circs;
+    uint64_t total_amps = 0;
+    uint32_t total_cb = 0;
+    int max_n = 0;
+    // device buffers (grown as needed)
+    qk::BOp *d_ops = nullptr;
+    size_t cap_ops = 0;
+    qk::BCirc *d_circs = nullptr;
+    size_t cap_circs = 0;
+    float2 *d_states = nullptr;
+    size_t cap_states = 0;
+    uint8_t *d_cbits = nullptr;
+    size_t cap_cbits = 0;
+    // pinned staging for the uploads (valid until the next run)
+    void *h_stage = nullptr;
+    size_t cap_stage = 0;
+    cudaEvent_t done = nullptr;
+    bool store_state = true;
+    std::string err;
+};
+
+namespace {
+
+qk_status bfail(qk_batch *b, qk_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    return s;
+}
+
+bool cur_circuit(qk_batch *b, qk::BCirc **c) {
+    if (b->circs.empty()) return false;
+    *c = &b->circs.back();
+    return true;
+}
+
+template <typename T>
+qk_status grow(qk_batch *b, T **p, size_t *cap, size_t need) {
+    if (need <= *cap) return QK_OK;
+    size_t nc = std::max(need, *cap * 2);
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc((void **)p, sizeof(T) * nc) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, QK_ENOMEM, "batch: cannot allocate %zu bytes", sizeof(T) * nc);
+    }
+    *cap = nc;
+    return QK_OK;
+}
+
+bool fill_cond(qk::BOp &op, const qk::BCirc &c, const int *cond, int ncc) {
+    if (ncc < 0 || ncc > 4 || (ncc > 0 && !cond)) return false;
+    op.ncond = (uint8_t)ncc;
+    for (int k = 0; k < ncc; ++k) {
+        if (cond[k] < 0 || cond[k] >= (int)c.ncb) return false;
+        op.cond[k] = (uint8_t)cond[k];
+    }
+    return true;
+}
+
+bool distinct(const int *q, int k, int n) {
+    for (int a = 0; a < k; ++a) {
+        if (q[a] < 0 || q[a] >= n) return false;
+        for (int b2 = 0; b2 < a; ++b2)
+            if (q[a] == q[b2]) return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+qk_status qk_batch_create(qk_batch **out, void *cuda_stream) {
+    if (!out) return QK_EINVAL;
+    *out = nullptr;
+    qk_batch *b = new (std::nothrow) qk_batch();
+    if (!b) return QK_ENOMEM;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return QK_ECUDA;
+    }
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return QK_ECUDA;
+        }
+        b->own_stream = true;
+    }
+    if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+        qk_batch_destroy(b);
+        return QK_ECUDA;
+    }
+    *out = b;
+    return QK_OK;
+}
+
+qk_status qk_batch_destroy(qk_batch *b) {
+    if (!b) return QK_EINVAL;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    cudaFree(b->d_ops);
+    cudaFree(b->d_circs);
+    cudaFree(b->d_states);
+    cudaFree(b->d_cbits);
+    if (b->h_stage) cudaFreeHost(b->h_stage);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return QK_OK;
+}
+
+qk_status qk_batch_clear(qk_batch *b) {
+    if (!b) return QK_EINVAL;
+    // the previous run may still read the staging buffer and device program
+    if (cudaEventSynchronize(b->done) != cudaSuccess) return bfail(b, QK_ECUDA, "batch: event wait failed");
+    b->ops.clear();
+    b->circs.clear();
+    b->total_amps = 0;
+    b->total_cb = 0;
+    b->max_n = 0;
+    return QK_OK;
+}
+
+qk_status qk_batch_add_circuit(qk_batch *b, int n, int ncbits, int *index) {
+    if (!b) return QK_EINVAL;
+    if (n < 1 || n > qk::kBMaxQubits) return bfail(b, QK_EINVAL, "batch: circuits take 1..%d qubits", qk::kBMaxQubits);
+    if (ncbits < 0 || ncbits > qk::kBMaxCbits) return bfail(b, QK_EINVAL, "batch: at most %d cbits", qk::kBMaxCbits);
+    qk::BCirc c{};
+    c.op_begin = c.op_end = (uint32_t)b->ops.size();
+    c.n = (uint32_t)n;
+    c.ncb = (uint32_t)ncbits;
+    c.cb_off = b->total_cb;
+    c.state_off = b->total_amps;
+    b->total_cb += (uint32_t)ncbits;
+    b->total_amps += 1ull << n;
+    b->max_n = std::max(b->max_n, n);
+    if (index) *index = (int)b->circs.size();
+    b->circs.push_back(c);
+    return QK_OK;
+}
+
+qk_status qk_batch_apply_gate(qk_batch *b, int gate_id, const int *targets, int nt, const int *controls, int nc,
+                              const int *cond_cbits, int ncc, const double *params, int np) {
+    if (!b) return QK_EINVAL;
+    qk::BCirc *c;
+    if (!cur_circuit(b, &c)) return bfail(b, QK_ESTATE, "batch: add a circuit first");
+    const int n = (int)c->n;
+    qk::cd m[4];
+    int ntg = 0;
+    if (!qk::builtin_matrix(gate_id, params, np, m, ntg) || nt != ntg || ntg != 1)
+        return bfail(b, QK_EINVAL, "batch: gate %d is not a 1-target built-in with these params", gate_id);
+    if (!distinct(targets, nt, n) || nc < 0 || nc > 16 || (nc > 0 && !distinct(controls, nc, n)))
+        return bfail(b, QK_EINVAL, "batch: bad qubit lists");
+    uint32_t cmask = 0;
+    for (int k = 0; k < nc; ++k) {
+        if (controls[k] == targets[0]) return bfail(b, QK_EINVAL, "batch: control equals target");
+        cmask |= 1u << controls[k];
+    }
+    qk::BOp op;
+    std::memset(&op, 0, sizeof op);
+    if (!fill_cond(op, *c, cond_cbits, ncc)) return bfail(b, QK_EINVAL, "batch: bad classical condition");
+    const int q = targets[0];
+    if (m[1] == 0.0 && m[2] == 0.0) {  // diagonal: one phase op per entry that is not 1
+        for (int e = 0; e < 2; ++e) {
+            const qk::cd f = e ? m[3] : m[0];
+            if (f == 1.0) continue;
+            qk::BOp p = op;
+            p.kind = qk::B_PHASE;
+            p.cmask = cmask | (1u << q);
+            p.val = cmask | (e ? (1u << q) : 0u);
+            p.ph.re = (float)f.real();
+            p.ph.im = (float)f.imag();
+            b->ops.push_back(p);
+        }
+    } else {
+        op.kind = qk::B_U2;
+        op.q = (uint8_t)q;
+        op.cmask = cmask;
+        for (int e = 0; e < 4; ++e) {
+            op.m[2 * e] = (float)m[e].real();
+            op.m[2 * e + 1] = (float)m[e].imag();
+        }
+        b->ops.push_back(op);
+    }
+    c->op_end = (uint32_t)b->ops.size();
+    return QK_OK;
+}
+
+qk_status qk_batch_apply_mulmod(qk_batch *b, const int *targets, int w, const int *controls, int nc, uint64_t cc,
+                                uint64_t N) {
+    if (!b) return QK_EINVAL;
+    qk::BCirc *c;
+    if (!cur_circuit(b, &c)) return bfail(b, QK_ESTATE, "batch: add a circuit first");
+    const int n = (int)c->n;
+    if (w < 1 || w > 16 || !distinct(targets, w, n) || nc < 0 || (nc > 0 && !distinct(controls, nc, n)))
+        return bfail(b, QK_EINVAL, "batch: bad mul-mod register or controls");
+    if (N < 2 || N > (1ull << w) || cc >= N) return bfail(b, QK_EINVAL, "batch: need 2 <= N <= 2^w and c < N");
+    bool ok = false;
+    const uint64_t inv = qk::modinv(cc, N, ok);
+    if (!ok) return bfail(b, QK_ENOTBIJECTIVE, "batch: gcd(c, N) != 1");
+    qk::BOp op;
+    std::memset(&op, 0, sizeof op);
+    op.kind = qk::B_MULMOD;
+    op.w = (uint8_t)w;
+    for (int k = 0; k < w; ++k) op.mm.rpos[k] = (uint8_t)targets[k];
+    for (int k = 0; k < nc; ++k) {
+        for (int t = 0; t < w; ++t)
+            if (controls[k] == targets[t]) return bfail(b, QK_EINVAL, "batch: control inside the register");
+        op.cmask |= 1u << controls[k];
+    }
+    op.mm.N = (uint32_t)N;
+    op.mm.cinv = (uint32_t)inv;
+    b->ops.push_back(op);
+    c->op_end = (uint32_t)b->ops.size();
+    return QK_OK;
+}
+
+qk_status qk_batch_measure(qk_batch *b, const int *qubits, int nq, const double *uniforms, const int *dest) {
+    if (!b) return QK_EINVAL;
+    qk::BCirc *c;
+    if (!cur_circuit(b, &c)) return bfail(b, QK_ESTATE, "batch: add a circuit first");
+    if (nq < 1 || !distinct(qubits, nq, (int)c->n) || !uniforms) return bfail(b, QK_EINVAL, "batch: bad qubit list");
+    for (int k = 0; k < nq; ++k) {
+        if (!(uniforms[k] >= 0.0 && uniforms[k] < 1.0)) return bfail(b, QK_EINVAL, "batch: uniform not in [0, 1)");
+        if (dest && (dest[k] < 0 || dest[k] >= (int)c->ncb)) return bfail(b, QK_EINVAL, "batch: bad destination cbit");
+        qk::BOp op;
+        std::memset(&op, 0, sizeof op);
+        op.kind = qk::B_MEASURE;
+        op.q = (uint8_t)qubits[k];
+        op.ms.u = uniforms[k];
+        op.ms.dest = dest ? dest[k] : -1;
+        b->ops.push_back(op);
+    }
+    c->op_end = (uint32_t)b->ops.size();
+    return QK_OK;
+}
+
+qk_status qk_batch_run(qk_batch *b, int store_states) {
+    if (!b) return QK_EINVAL;
+    if (b->circs.empty()) return QK_OK;
+    b->store_state = store_states != 0;
+    qk_status s;
+    if ((s = grow(b, &b->d_ops, &b->cap_ops, std::max<size_t>(1, b->ops.size()))) != QK_OK) return s;
+    if ((s = grow(b, &b->d_circs, &b->cap_circs, b->circs.size())) != QK_OK) return s;
+    if (b->store_state && (s = grow(b, &b->d_states, &b->cap_states, b->total_amps)) != QK_OK) return s;
+    if ((s = grow(b, &b->d_cbits, &b->cap_cbits, std::max<size_t>(1, b->total_cb))) != QK_OK) return s;
+    // stage the program in pinned memory so that the copies are truly asynchronous
+    const size_t ob = sizeof(qk::BOp) * b->ops.size(), cb = sizeof(qk::BCirc) * b->circs.size();
+    if (ob + cb > b->cap_stage) {
+        if (b->h_stage) cudaFreeHost(b->h_stage);
+        b->h_stage = nullptr;
+        b->cap_stage = 0;
+        if (cudaMallocHost(&b->h_stage, (ob + cb) * 2) != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, QK_ENOMEM, "batch: cannot allocate pinned staging");
+        }
+        b->cap_stage = (ob + cb) * 2;
+    }
+    // circuits sorted by size: one launch per qubit count, each sized to its
+    // shared memory (small circuits then share an SM)
+    std::vector<qk::BCirc> sorted(b->circs);
+    std::stable_sort(sorted.begin(), sorted.end(), [](const qk::BCirc &x, const qk::BCirc &y) { return x.n < y.n; });
+    std::memcpy(b->h_stage, b->ops.data(), ob);
+    std::memcpy((char *)b->h_stage + ob, sorted.data(), cb);
+    if (cudaMemcpyAsync(b->d_ops, b->h_stage, ob, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_circs, (char *)b->h_stage + ob, cb, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        return bfail(b, QK_ECUDA, "batch: upload failed");
+    const size_t max_smem = sizeof(float2) * 2 * ((size_t)1 << b->max_n);
+    if (max_smem > 48 * 1024 &&
+        cudaFuncSetAttribute(qk::k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem) != cudaSuccess)
+        return bfail(b, QK_ECUDA, "batch: shared memory attribute failed");
+    for (size_t i = 0; i < sorted.size();) {
+        size_t j = i;
+        while (j < sorted.size() && sorted[j].n == sorted[i].n) ++j;
+        const size_t smem = sizeof(float2) * 2 * ((size_t)1 << sorted[i].n);
+        qk::k_batch<<<(unsigned)(j - i), qk::kBThreads, smem, b->stream>>>(b->d_circs + i, b->d_ops, b->d_states,
+                                                                          b->d_cbits, b->store_state ? 1 : 0);
+        if (cudaGetLastError() != cudaSuccess) return bfail(b, QK_ECUDA, "batch: launch failed");
+        i = j;
+    }
+    if (cudaEventRecord(b->done, b->stream) != cudaSuccess) return bfail(b, QK_ECUDA, "batch: event record failed");
+    return QK_OK;
+}
+
+int qk_batch_done(qk_batch *b) {
+    if (!b) return -1;
+    const cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) {
+        cudaGetLastError();
+        return 0;
+    }
+    return -1;
+}
+
+qk_status qk_batch_read(qk_batch *b, int circuit, uint8_t *cbits, int ncb, void *state, size_t bytes) {
+    if (!b) return QK_EINVAL;
+    if (circuit < 0 || circuit >= (int)b->circs.size()) return bfail(b, QK_EINVAL, "batch: bad circuit index");
+    const qk::BCirc &c = b->circs[circuit];
+    if (ncb < 0 || ncb > (int)c.ncb || (ncb > 0 && !cbits)) return bfail(b, QK_EINVAL, "batch: bad cbit count");
+    if (state && (!b->store_state || bytes != sizeof(float2) << c.n))
+        return bfail(b, QK_EINVAL, "batch: state not stored or wrong size (%zu bytes expected)", sizeof(float2) << c.n);
+    if (cudaEventSynchronize(b->done) != cudaSuccess) return bfail(b, QK_ECUDA, "batch: event wait failed");
+    if (ncb > 0 && cudaMemcpy(cbits, b->d_cbits + c.cb_off, ncb, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bfail(b, QK_ECUDA, "batch: cbit copy failed");
+    if (state && cudaMemcpy(state, b->d_states + c.state_off, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bfail(b, QK_ECUDA, "batch: state copy failed");
+    return QK_OK;
+}
+
+qk_status qk_batch_read_all_cbits(qk_batch *b, uint8_t *out, size_t n) {
+    if (!b) return QK_EINVAL;
+    if (n != b->total_cb || (n > 0 && !out)) return bfail(b, QK_EINVAL, "batch: need %u cbit bytes", b->total_cb);
+    if (cudaEventSynchronize(b->done) != cudaSuccess) return bfail(b, QK_ECUDA, "batch: event wait failed");
+    if (n > 0 && cudaMemcpy(out, b->d_cbits, n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bfail(b, QK_ECUDA, "batch: cbit copy failed");
+    return QK_OK;
+}
+
+int qk_batch_num_circuits(const qk_batch *b) { return b ? (int)b->circs.size() : -1; }
+
+const char *qk_batch_last_error(const qk_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+}  // extern "C"

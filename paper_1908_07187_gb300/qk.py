@@ -78,6 +78,21 @@ _SIGS = {
     "qk_capture_end": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
     "qk_graph_launch": ([_P], ctypes.c_int),
     "qk_graph_destroy": ([_P], ctypes.c_int),
+    "qk_batch_create": ([ctypes.POINTER(_P), _P], ctypes.c_int),
+    "qk_batch_destroy": ([_P], ctypes.c_int),
+    "qk_batch_clear": ([_P], ctypes.c_int),
+    "qk_batch_add_circuit": ([_P, ctypes.c_int, ctypes.c_int, _IP], ctypes.c_int),
+    "qk_batch_apply_gate": ([_P, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int, _IP, ctypes.c_int, _DP,
+                             ctypes.c_int], ctypes.c_int),
+    "qk_batch_apply_mulmod": ([_P, _IP, ctypes.c_int, _IP, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64],
+                              ctypes.c_int),
+    "qk_batch_measure": ([_P, _IP, ctypes.c_int, _DP, _IP], ctypes.c_int),
+    "qk_batch_run": ([_P, ctypes.c_int], ctypes.c_int),
+    "qk_batch_done": ([_P], ctypes.c_int),
+    "qk_batch_read": ([_P, ctypes.c_int, _U8P, ctypes.c_int, _P, ctypes.c_size_t], ctypes.c_int),
+    "qk_batch_read_all_cbits": ([_P, _U8P, ctypes.c_size_t], ctypes.c_int),
+    "qk_batch_num_circuits": ([_P], ctypes.c_int),
+    "qk_batch_last_error": ([_P], ctypes.c_char_p),
     "qk_last_error": ([_P], ctypes.c_char_p),
     "qk_status_str": ([ctypes.c_int], ctypes.c_char_p),
 }
@@ -320,6 +335,104 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many small circuits (n <= 13) run in one launch (qk_batch_*)."""
+
+    MAX_QUBITS = 13
+
+    def __init__(self, stream: Optional[int] = None):
+        h = _P()
+        st = _lib.qk_batch_create(ctypes.byref(h), _P(stream) if stream else None)
+        if st != QK_OK:
+            raise QKError(st, "qk_batch_create failed")
+        self._h = h
+        self._ncb: list = []
+        self._n: list = []
+
+    def _check(self, st: int):
+        if st != QK_OK:
+            raise QKError(st, _lib.qk_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.qk_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def clear(self):
+        self._check(_lib.qk_batch_clear(self._h))
+        self._ncb, self._n = [], []
+
+    def add_circuit(self, n: int, ncbits: int = 0) -> int:
+        idx = ctypes.c_int(0)
+        self._check(_lib.qk_batch_add_circuit(self._h, n, ncbits, ctypes.byref(idx)))
+        self._ncb.append(ncbits)
+        self._n.append(n)
+        return idx.value
+
+    def apply_gate(self, gate, targets, controls=(), cond=(), params=()):
+        gid = GATE[gate] if isinstance(gate, str) else int(gate)
+        t, nt = _ints(targets)
+        c, nc = _ints(controls)
+        k, nk = _ints(cond)
+        p = (ctypes.c_double * max(1, len(params)))(*params)
+        self._check(_lib.qk_batch_apply_gate(self._h, gid, t, nt, c, nc, k, nk, p, len(params)))
+
+    def apply_mulmod(self, targets, controls, c: int, N: int):
+        t, nt = _ints(targets)
+        cl, nc = _ints(controls)
+        self._check(_lib.qk_batch_apply_mulmod(self._h, t, nt, cl, nc, c, N))
+
+    def measure(self, qubits, uniforms, dest=None):
+        q, nq = _ints(qubits)
+        u = (ctypes.c_double * max(1, nq))(*uniforms)
+        d = _ints(dest)[0] if dest else None
+        self._check(_lib.qk_batch_measure(self._h, q, nq, u, d))
+
+    def add_ops(self, n: int, ncbits: int, ops) -> int:
+        """A workloads circuit's ops as one batch circuit (marshalling only)."""
+        idx = self.add_circuit(n, ncbits)
+        for op in ops:
+            if op.kind == "measure":
+                self.measure(op.targets, op.uniforms, op.cbits or None)
+            elif op.kind == "mulmod":
+                a, j, N = (int(x) for x in op.params)
+                if op.cond:
+                    raise ValueError("batched mul-mod takes no classical condition")
+                self.apply_mulmod(op.targets, op.controls, pow(a, 1 << j, N), N)
+            else:
+                self.apply_gate(op.kind, op.targets, op.controls, op.cond, op.params)
+        return idx
+
+    def run(self, store_states: bool = True):
+        self._check(_lib.qk_batch_run(self._h, 1 if store_states else 0))
+
+    def done(self) -> bool:
+        r = _lib.qk_batch_done(self._h)
+        if r < 0:
+            raise QKError(QK_ECUDA, "batch run failed")
+        return r == 1
+
+    def read(self, circuit: int, state: bool = True):
+        ncb = self._ncb[circuit]
+        cb = np.zeros(max(1, ncb), dtype=np.uint8)
+        st = np.empty(1 << self._n[circuit], dtype=np.complex64) if state else None
+        self._check(_lib.qk_batch_read(self._h, circuit, cb.ctypes.data_as(_U8P), ncb,
+                                       st.ctypes.data if state else None, st.nbytes if state else 0))
+        return cb[:ncb], st
+
+    def read_all_cbits(self) -> np.ndarray:
+        tot = sum(self._ncb)
+        out = np.zeros(max(1, tot), dtype=np.uint8)
+        self._check(_lib.qk_batch_read_all_cbits(self._h, out.ctypes.data_as(_U8P), tot))
+        return out[:tot]
 
 
 def run_ops(ctx: Context, ops) -> None:

@@ -1,0 +1,105 @@
+"""Batched small circuits (one CTA per circuit, one launch per batch) against the
+oracle and the per-gate engine; each result is the same alone and in the mix."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+MARGIN = 1e-6
+
+
+@pytest.fixture(scope="module")
+def qk():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_07187_gb300 import qk as mod
+
+    return mod
+
+
+def requests(count, seed0=100, n_max=13):
+    return [workloads.serving_request(seed0 + i, n_min=3, n_max=n_max) for i in range(count)]
+
+
+def oracle_margins_ok(circ, ref):
+    """True when no measured uniform lies within MARGIN of its P0."""
+    st = oracle.OracleState(circ.n_qubits, circ.n_cbits)
+    for op in circ.ops:
+        if op.kind == "measure":
+            p0 = st.prob0(op.targets[0])
+            if abs(op.uniforms[0] - p0) < MARGIN:
+                return False
+        st.apply_op(op)
+    return True
+
+
+def test_batch_matches_oracle_and_engine(qk):
+    reqs = requests(40)
+    b = qk.Batch()
+    for c in reqs:
+        b.add_ops(c.n_qubits, c.n_cbits, c.ops)
+    b.run()
+    for i, c in enumerate(reqs):
+        bits, psi = b.read(i)
+        ref = oracle.run_circuit(c)
+        if not oracle_margins_ok(c, ref):
+            continue
+        assert list(bits) == [int(x) for x in ref.cbits], c.name
+        assert np.max(np.abs(psi.astype(np.complex128) - ref.psi)) < 1e-4, c.name
+        ctx = qk.run_circuit(c, "c64", "fused")
+        assert list(ctx.read_cbits()) == list(bits), c.name
+        ctx.close()
+    b.close()
+
+
+def test_batch_result_is_the_same_alone_and_in_the_mix(qk):
+    reqs = requests(24, seed0=500)
+    mix = qk.Batch()
+    for c in reqs:
+        mix.add_ops(c.n_qubits, c.n_cbits, c.ops)
+    mix.run()
+    alone = qk.Batch()
+    for i, c in enumerate(reqs):
+        alone.clear()
+        alone.add_ops(c.n_qubits, c.n_cbits, c.ops)
+        alone.run()
+        b1, s1 = alone.read(0)
+        b2, s2 = mix.read(i)
+        assert list(b1) == list(b2)
+        assert np.array_equal(s1, s2)   # same kernel, same order of operations: bit-identical
+    mix.close()
+    alone.close()
+
+
+def test_batch_mulmod_and_conditions(qk):
+    n = 12
+    rng = np.random.default_rng(4)
+    b = qk.Batch()
+    b.add_circuit(n, 2)
+    ref = oracle.OracleState(n, 2)
+    for q in range(n):
+        b.apply_gate("h", [q])
+        ref.apply_matrix(oracle.GATES_1Q["h"], [q])
+    b.apply_mulmod(list(range(1, 11)), [0], 7, 1001)
+    ref.apply_mulmod(7, 1001, list(range(1, 11)), [0])
+    b.measure([3], [0.3], [1])
+    ref.measure([3], [0.3], [1])
+    b.apply_gate("x", [5], cond=[1])
+    if ref.cbits[1]:
+        ref.apply_matrix(oracle.GATES_1Q["x"], [5])
+    b.apply_gate("u3", [2], controls=[7, 9], params=[0.1, 0.2, 0.3])
+    ref.apply_matrix(oracle.u3(0.1, 0.2, 0.3), [2], [7, 9])
+    b.run()
+    bits, psi = b.read(0)
+    assert list(bits) == [int(x) for x in ref.cbits]
+    assert np.max(np.abs(psi - ref.psi)) < 1e-5
+    with pytest.raises(qk.QKError):
+        b.add_circuit(14, 0)
+    with pytest.raises(qk.QKError):
+        b.apply_mulmod([1, 2, 3], [0], 5, 15)   # N > 2^w
+    b.close()

@@ -285,6 +285,56 @@ def paper_stage_count(N: int) -> int:
     return (N * N - 1).bit_length()
 
 
+def serving_request(seed: int, n: int | None = None, n_min: int = 8, n_max: int = 33) -> Circuit:
+    """One serving request: n qubits (log-uniform in [n_min, n_max] unless given),
+    5..40 layers cycling U3-on-every-qubit / CZ-even / CZ-odd, one controlled
+    x -> a^(2^j) x mod N oracle on a w-qubit register (w in 10..16, only when
+    n >= w + 1: control qubit 0, register qubits 1..w with qubit 1 the MSB), and
+    1..4 mid-circuit measurements, each into its own cbit and followed by a U3 on
+    another qubit conditioned on that cbit."""
+    rng = SplitMix64(seed * 2654435761 + 17)
+    if n is None:
+        n = int(round(math.exp(math.log(n_min) + rng.uniform() * (math.log(n_max) - math.log(n_min)))))
+    n_layers = 5 + rng.below(36)
+    w = 10 + rng.below(7)
+    oracle_at = rng.below(n_layers) if n >= w + 1 else -1
+    n_meas = 1 + rng.below(4)
+    meas_at = sorted(rng.below(n_layers) for _ in range(n_meas))
+    ops: List[Op] = []
+    k = 0
+    for layer in range(n_layers):
+        kind = layer % 3
+        if kind == 0:
+            ops += [_u3_op(rng, q) for q in range(n)]
+        else:
+            start = 0 if kind == 1 else 1
+            ops += [Op("z", (q + 1,), controls=(q,)) for q in range(start, n - 1, 2)]
+        if layer == oracle_at:
+            while True:
+                N = (1 << (w - 1)) | rng.below(1 << (w - 1)) | 1
+                a = 2 + rng.below(N - 3)
+                if math.gcd(a, N) == 1:
+                    break
+            ops.append(Op("mulmod", tuple(range(1, w + 1)), controls=(0,), params=(a, rng.below(2 * w), N)))
+        while k < n_meas and meas_at[k] == layer:
+            q = rng.below(n)
+            t = (q + 1 + rng.below(n - 1)) % n
+            ops.append(Op("measure", (q,), cbits=(k,), uniforms=(rng.uniform(),)))
+            ops.append(Op("u3", (t,), params=(rng.angle(), rng.angle(), rng.angle()), cond=(k,)))
+            k += 1
+    return Circuit(n, n_meas, ops, name=f"request{seed}_n{n}")
+
+
+def poisson_arrivals(count: int, rate_per_s: float, seed: int = 7):
+    """Arrival times (seconds from 0) of a Poisson process with the given rate."""
+    rng = SplitMix64(seed)
+    t, out = 0.0, []
+    for _ in range(count):
+        t += -math.log(1.0 - rng.uniform()) / rate_per_s
+        out.append(t)
+    return out
+
+
 def random_state(n: int, seed: int):
     """Seeded random normalised complex128 state (numpy array) for parity inputs:
     independent standard normal real and imaginary parts (numpy PCG64), normalised."""

@@ -85,8 +85,8 @@ def test_batch_mulmod_and_conditions(qk):
     for q in range(n):
         b.apply_gate("h", [q])
         ref.apply_matrix(oracle.GATES_1Q["h"], [q])
-    b.apply_mulmod(list(range(1, 11)), [0], 7, 1001)
-    ref.apply_mulmod(7, 1001, list(range(1, 11)), [0])
+    b.apply_mulmod(list(range(1, 11)), [0], 5, 1001)   # gcd(5, 7*11*13) = 1
+    ref.apply_mulmod(5, 1001, list(range(1, 11)), [0])
     b.measure([3], [0.3], [1])
     ref.measure([3], [0.3], [1])
     b.apply_gate("x", [5], cond=[1])

@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-pass-per-gate comparison")
     ap.add_argument("--no-kitaev", action="store_true", help="skip the Kitaev order-finding measurement")
     ap.add_argument("--no-block", action="store_true", help="skip the dense 5-qubit block measurement")
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -343,6 +344,30 @@ def kitaev_measurement(qk, torch, stream, b: int = 20, reps: int = 5):
 
 
 # ---------------------------------------------------------------------------
+# serving (secondary measurement)
+# ---------------------------------------------------------------------------
+def serving_measurement(torch, count: int, rate: float = 200.0):
+    """Seeded requests of 8..33 qubits (log-uniform) arriving as a Poisson process,
+    served with continuous batching vs one at a time on the plain sequential path.
+    Measured bits of the two paths must agree."""
+    from paper_1908_07187_gb300 import qk, serve
+
+    reqs = [workloads.serving_request(10_000 + i) for i in range(count)]
+    arr = workloads.poisson_arrivals(count, rate, seed=11)
+    warm = [workloads.serving_request(20_000 + i, n_min=8, n_max=20) for i in range(8)]
+    serve.Server(qk, torch).run(warm, [0.0] * len(warm))
+    served = serve.Server(qk, torch).run(reqs, arr)
+    plain = serve.serve_plain(qk, torch, reqs, arr)
+    agree = sum(list(a.cbits) == list(b.cbits) for a, b in zip(served, plain))
+    out = {"requests": count, "arrival_rate_per_s": rate, "qubits": "log-uniform 8..33",
+           "served": serve.summarize(served), "plain": serve.summarize(plain),
+           "small_batched": sum(r.path == "batch" for r in served), "bits_agree": agree,
+           "hbm_budget_bytes": 160 * 10**9}
+    out["speedup_circuits_per_s"] = out["served"]["circuits_per_s"] / out["plain"]["circuits_per_s"]
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def main():
@@ -489,6 +514,9 @@ def main():
     block = None
     if not args.no_block:
         block = block_measurement(qk, torch, stream, n)
+    serving = None
+    if args.serve_requests > 0 and world == 1:
+        serving = serving_measurement(torch, args.serve_requests)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -511,6 +539,7 @@ def main():
             "plain_path": plain,
             "kitaev": kitaev,
             "block5": block,
+            "serving": serving,
             "launch_profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items() if v["launches"]},
             "clocks": clk,
         }

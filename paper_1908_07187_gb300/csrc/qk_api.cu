@@ -116,6 +116,19 @@ qk_status fail(qk_ctx *c, qk_status s, const char *fmt, ...) {
 
 size_t full_pass_bytes(const qk_ctx *c) { return (size_t)2 * c->amp << c->n; }
 
+// Device memory is stream-ordered on the context's stream (cudaMallocAsync /
+// cudaFreeAsync): freeing a finished context does not synchronise the device, so
+// other contexts' work keeps running (the serving loop relies on this).
+cudaError_t dalloc(qk_ctx *c, void **p, size_t bytes) { return cudaMallocAsync(p, bytes, c->stream); }
+void dfree(qk_ctx *c, void *p) {
+    if (p) cudaFreeAsync(p, c->stream);
+}
+// host -> device copy of a small pageable buffer, complete before return
+cudaError_t upload(qk_ctx *c, void *dst, const void *src, size_t bytes) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(c->stream) : e;
+}
+
 cudaEvent_t get_event(qk_ctx *c) {
     if (!c->ev_pool.empty()) {
         cudaEvent_t e = c->ev_pool.back();
@@ -196,8 +209,8 @@ qk_status upload_matrix(qk_ctx *c, const std::vector<cd> &m, void **dptr) {
             memcpy(&host[i * 16], v, 16);
         }
     }
-    CUDA_TRY(c, cudaMalloc(dptr, host.size()));
-    CUDA_TRY(c, cudaMemcpy(*dptr, host.data(), host.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, dalloc(c, dptr, host.size()));
+    CUDA_TRY(c, upload(c, *dptr, host.data(), host.size()));
     return QK_OK;
 }
 
@@ -303,12 +316,12 @@ qk_status apply_1q(qk_ctx *c, const cd m[4], int q, uint64_t cmask, const qk::Co
 qk_status ensure_scratch(qk_ctx *c) {
     if (c->d_scratch && c->scratch_bytes == c->state_bytes) return QK_OK;
     if (c->capturing) return fail(c, QK_ESTATE, "a gather buffer would be allocated during capture");
-    if (c->d_scratch) cudaFree(c->d_scratch);
+    dfree(c, c->d_scratch);
     c->d_scratch = nullptr;
     c->scratch_bytes = 0;
     if (c->opt.hbm_budget_bytes && 2 * c->state_bytes > c->opt.hbm_budget_bytes)
         return fail(c, QK_EBUDGET, "permutation scratch (%zu bytes) exceeds the HBM budget", c->state_bytes);
-    if (cudaMalloc(&c->d_scratch, c->state_bytes) != cudaSuccess) {
+    if (dalloc(c, &c->d_scratch, c->state_bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, QK_ENOMEM, "cannot allocate %zu bytes of permutation scratch", c->state_bytes);
     }
@@ -339,10 +352,10 @@ qk_status canonicalize(qk_ctx *c) {
 qk_status ensure_slots(qk_ctx *c, int nq) {
     if (nq <= c->slot_cap) return QK_OK;
     if (c->capturing) return fail(c, QK_ESTATE, "measurement slots would be allocated during capture");
-    if (c->d_slots) cudaFree(c->d_slots);
+    dfree(c, c->d_slots);
     c->d_slots = nullptr;
     int cap = std::max(nq, 64);
-    CUDA_TRY(c, cudaMalloc(&c->d_slots, sizeof(qk::MeasSlot) * cap));
+    CUDA_TRY(c, dalloc(c, (void **)&c->d_slots, sizeof(qk::MeasSlot) * cap));
     c->slot_cap = cap;
     return QK_OK;
 }
@@ -382,9 +395,9 @@ qk_status apply_block_tc(qk_ctx *c, int gate_id, const int *targets, uint32_t ke
                     bl[idx[q]] = vals[q] - hi;
                 }
             }
-        CUDA_TRY(c, cudaMalloc(&dev, sizeof(float) * 2 * 64 * 64));
-        CUDA_TRY(c, cudaMemcpy(dev, bh.data(), sizeof(float) * 64 * 64, cudaMemcpyHostToDevice));
-        CUDA_TRY(c, cudaMemcpy(dev + 64 * 64, bl.data(), sizeof(float) * 64 * 64, cudaMemcpyHostToDevice));
+        CUDA_TRY(c, dalloc(c, (void **)&dev, sizeof(float) * 2 * 64 * 64));
+        CUDA_TRY(c, upload(c, dev, bh.data(), sizeof(float) * 64 * 64));
+        CUDA_TRY(c, upload(c, dev + 64 * 64, bl.data(), sizeof(float) * 64 * 64));
         g.tc_cache.push_back({key, dev});
     }
     LaunchScope ls(c, 3, (double)full_pass_bytes(c));
@@ -464,8 +477,9 @@ qk_status qk_create(qk_ctx **out, qk_precision precision, void *cuda_stream, con
         c->own_stream = true;
     }
     c->meas_blocks = c->sms * kMeasBlocksPerSM;
-    if (cudaMalloc(&c->d_partials, sizeof(double) * 2 * c->meas_blocks) != cudaSuccess ||
-        cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+    if (dalloc(c, (void **)&c->d_partials, sizeof(double) * 2 * c->meas_blocks) != cudaSuccess ||
+        dalloc(c, (void **)&c->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream) != cudaSuccess) {
         cudaGetLastError();
         qk_destroy(c);
         return QK_ENOMEM;
@@ -483,17 +497,18 @@ qk_status qk_destroy(qk_ctx *c) {
     for (auto &p : c->prof) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (auto &g : c->gates) {
-        if (g.d_mat) cudaFree(g.d_mat);
-        if (g.d_finv) cudaFree(g.d_finv);
-        for (auto &e : g.tc_cache) cudaFree(e.second);
+        dfree(c, g.d_mat);
+        dfree(c, g.d_finv);
+        for (auto &e : g.tc_cache) dfree(c, e.second);
     }
-    if (c->d_err) cudaFree(c->d_err);
-    if (c->d_swap_mat) cudaFree(c->d_swap_mat);
-    if (c->d_state) cudaFree(c->d_state);
-    if (c->d_scratch) cudaFree(c->d_scratch);
-    if (c->d_cbits) cudaFree(c->d_cbits);
-    if (c->d_partials) cudaFree(c->d_partials);
-    if (c->d_slots) cudaFree(c->d_slots);
+    dfree(c, c->d_err);
+    dfree(c, c->d_swap_mat);
+    dfree(c, c->d_state);
+    dfree(c, c->d_scratch);
+    dfree(c, c->d_cbits);
+    dfree(c, c->d_partials);
+    dfree(c, c->d_slots);
+    if (c->stream) cudaStreamSynchronize(c->stream);   // this stream only
     if (c->planner) qk::free_planner(c->planner);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -513,20 +528,19 @@ qk_status qk_add_qubits(qk_ctx *c, int k, int *first) {
     if (c->opt.hbm_budget_bytes && bytes > c->opt.hbm_budget_bytes)
         return fail(c, QK_EBUDGET, "state of %d qubits (%zu bytes) exceeds the HBM budget", nn, bytes);
     void *d = nullptr;
-    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    if (dalloc(c, &d, bytes) != cudaSuccess) {
         cudaGetLastError();
         return fail(c, QK_ENOMEM, "cannot allocate %zu bytes for %d qubits", bytes, nn);
     }
     CUDA_TRY(c, cudaMemsetAsync(d, 0, bytes, c->stream));
     if (c->d_state) {
         CUDA_TRY(c, cudaMemcpyAsync(d, c->d_state, c->state_bytes, cudaMemcpyDeviceToDevice, c->stream));
-        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-        cudaFree(c->d_state);
+        dfree(c, c->d_state);
     } else {
         CUDA_TRY(c, qk::launch_set_basis((int)c->prec, d, 0, c->stream));
     }
     if (c->d_scratch) {
-        cudaFree(c->d_scratch);
+        dfree(c, c->d_scratch);
         c->d_scratch = nullptr;
         c->scratch_bytes = 0;
     }
@@ -545,12 +559,11 @@ qk_status qk_add_cbits(qk_ctx *c, int k, int *first) {
     if (c->ncb + k > c->cb_cap) {
         int cap = std::max(c->ncb + k, std::max(64, 2 * c->cb_cap));
         uint8_t *d = nullptr;
-        CUDA_TRY(c, cudaMalloc(&d, cap));
+        CUDA_TRY(c, dalloc(c, (void **)&d, cap));
         CUDA_TRY(c, cudaMemsetAsync(d, 0, cap, c->stream));
         if (c->d_cbits) {
             CUDA_TRY(c, cudaMemcpyAsync(d, c->d_cbits, c->ncb, cudaMemcpyDeviceToDevice, c->stream));
-            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-            cudaFree(c->d_cbits);
+            dfree(c, c->d_cbits);
         }
         c->d_cbits = d;
         c->cb_cap = cap;
@@ -625,8 +638,8 @@ qk_status qk_define_gate_perm_table(qk_ctx *c, int w, const uint64_t *f, int *ga
     GateDef g;
     g.kind = 2;
     g.k = w;
-    CUDA_TRY(c, cudaMalloc(&g.d_finv, sizeof(uint32_t) * d));
-    CUDA_TRY(c, cudaMemcpy(g.d_finv, inv.data(), sizeof(uint32_t) * d, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, dalloc(c, (void **)&g.d_finv, sizeof(uint32_t) * d));
+    CUDA_TRY(c, upload(c, g.d_finv, inv.data(), sizeof(uint32_t) * d));
     *gate_id = (int)c->gates.size();
     c->gates.push_back(std::move(g));
     return QK_OK;
@@ -983,9 +996,10 @@ qk_status qk_sync(qk_ctx *c) {
     if (s != QK_OK) return s;
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     int err = 0;
-    CUDA_TRY(c, cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (err) {
-        CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
+        CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
         return fail(c, QK_ETIMEOUT, "a tensor-core pass gave up a bounded wait; the state is not valid");
     }
     return QK_OK;

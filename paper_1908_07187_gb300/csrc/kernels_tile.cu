@@ -282,24 +282,67 @@ struct Pending {
     }
 };
 
-// One gate of a TOP_U2L layer on register bit K: fold the pending phase of bit
-// K into the matrix, then the butterflies.
+// Rotation butterfly on register bit K: (x0, x1) <- (c x0 + m01 x1, s x0 + m11 x1)
+// with c, s real and m01, m11 complex: 12 FP32 operations per amplitude pair.
+template <int K>
+__device__ __forceinline__ void rot_butterfly(Regs &v, float c, float s, float2 m01, float2 m11) {
+    const float n01i = -m01.y, n11i = -m11.y;
+    if constexpr (K == 0) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float ar = v.R[j].x, ai = v.I[j].x, br = v.R[j].y, bi = v.I[j].y;
+            v.R[j].x = fmaf(n01i, bi, fmaf(m01.x, br, c * ar));
+            v.I[j].x = fmaf(m01.y, br, fmaf(m01.x, bi, c * ai));
+            v.R[j].y = fmaf(n11i, bi, fmaf(m11.x, br, s * ar));
+            v.I[j].y = fmaf(m11.y, br, fmaf(m11.x, bi, s * ai));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j & (1 << (K - 1))) continue;
+            const int j1 = j | (1 << (K - 1));
+            const float2 A = v.R[j], B = v.I[j], C = v.R[j1], D = v.I[j1];
+            float2 r0, i0, r1, i1;
+            r0.x = fmaf(n01i, D.x, fmaf(m01.x, C.x, c * A.x));
+            r0.y = fmaf(n01i, D.y, fmaf(m01.x, C.y, c * A.y));
+            i0.x = fmaf(m01.y, C.x, fmaf(m01.x, D.x, c * B.x));
+            i0.y = fmaf(m01.y, C.y, fmaf(m01.x, D.y, c * B.y));
+            r1.x = fmaf(n11i, D.x, fmaf(m11.x, C.x, s * A.x));
+            r1.y = fmaf(n11i, D.y, fmaf(m11.x, C.y, s * A.y));
+            i1.x = fmaf(m11.y, C.x, fmaf(m11.x, D.x, s * B.x));
+            i1.y = fmaf(m11.y, C.y, fmaf(m11.x, D.y, s * B.y));
+            v.R[j] = r0; v.I[j] = i0; v.R[j1] = r1; v.I[j1] = i1;
+        }
+    }
+}
+
+// One gate of a TOP_U2L layer on register bit K, given in rotation form
+// U = e^{i a} diag(1, e^{i p}) [[c, -s], [s, c]] diag(1, e^{i l}) (m = c, s, then a, p,
+// l as 32-bit turns).  The right factor and the pending phase of bit K fold into the
+// butterfly, U diag(1, b) with b = e^{i l} times the pending factor; the left
+// factors become the new pending phases of bit K and of the whole thread (folded
+// into the next gate on that bit, or flushed at the next transpose).  A variant
+// that applied the left factor inside the butterfly when no later gate on the bit
+// follows measured slower: the second code path raised register spills.
 template <int K>
 __device__ __forceinline__ void layer_gate(Regs &v, Pending &pd, const float *m) {
-    float2 m00 = make_float2(m[0], m[1]), m01 = make_float2(m[2], m[3]);
-    float2 m10 = make_float2(m[4], m[5]), m11 = make_float2(m[6], m[7]);
-    if ((pd.mask & (1 << K)) && pd.t[K] != 0) {
-        const float2 ak = turns_to_phase(pd.t[K]);
-        m01 = cmul(m01, ak);
-        m11 = cmul(m11, ak);
+    const float c = m[0], s = m[1];
+    const uint32_t ta = __float_as_uint(m[2]), tp = __float_as_uint(m[3]);
+    uint32_t tb = __float_as_uint(m[4]);
+    if (pd.mask & (1 << K)) tb += pd.t[K];
+    float2 m01 = make_float2(-s, 0.f), m11 = make_float2(c, 0.f);
+    if (tb != 0) {
+        const float2 b = turns_to_phase(tb);
+        m01 = make_float2(-s * b.x, -s * b.y);
+        m11 = make_float2(c * b.x, c * b.y);
     }
-    pd.t[K] = 0;
-    pd.mask &= ~(1 << K);
-    if constexpr (K == 0) {
-        u2_bit0(v, m00, m01, m10, m11, 0);
-    } else {
-        const Mat M(m00, m01, m10, m11);
-        u2_packed<K>(v, M, 0);
+    rot_butterfly<K>(v, c, s, m01, m11);
+    pd.t[K] = tp;
+    if (tp != 0) pd.mask |= 1 << K;
+    else pd.mask &= ~(1 << K);
+    if (ta != 0) {
+        pd.t0 += ta;
+        pd.mask |= 32;
     }
 }
 

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <complex>
 #include <cstring>
 #include <vector>
 
@@ -118,6 +119,38 @@ void encode_cond(uint64_t mask, uint64_t val, int arr, const int *local_of, Tile
             t.tval |= (uint16_t)(bit << (5 + pos));
         }
     }
+}
+
+// A 2x2 unitary as e^{i a} diag(1, e^{i p}) [[c, -s], [s, c]] diag(1, e^{i l}) with c, s
+// real (c may be negative, s >= 0); the layer kernel stores c, s and a, p, l in 32-bit
+// fixed-point turns.  a is the phase of u00 folded into (-pi/2, pi/2] so that c =
+// e^{-i a} u00 is real; then u10 = e^{i a} s e^{i p}, u01 = -e^{i a} s e^{i l}, and
+// for s = 0 the phase of u11 / c fixes p (l = 0).
+uint32_t angle_turns(double x) {
+    double frac = x / (2.0 * M_PI);
+    frac -= std::floor(frac);
+    return (uint32_t)(uint64_t)std::llround(frac * 4294967296.0);
+}
+void rotation_form(const float *m, float *out) {
+    const std::complex<double> u00(m[0], m[1]), u01(m[2], m[3]), u10(m[4], m[5]), u11(m[6], m[7]);
+    double a = std::abs(u00) > 0 ? std::arg(u00) : 0.0;
+    if (a > M_PI / 2) a -= M_PI;
+    if (a <= -M_PI / 2) a += M_PI;
+    const std::complex<double> ea = std::polar(1.0, -a);
+    const double c = (u00 * ea).real();
+    const double s = std::abs(u10);
+    double p = 0.0, l = 0.0;
+    if (s > 0) {
+        p = std::arg(u10 * ea);
+        l = std::arg(-u01 * ea);
+    } else {
+        p = std::arg(u11 * ea / c);
+    }
+    const uint32_t t[3] = {angle_turns(a), angle_turns(p), angle_turns(l)};
+    out[0] = (float)c;
+    out[1] = (float)s;
+    std::memcpy(&out[2], t, sizeof t);
+    out[5] = out[6] = out[7] = 0.f;
 }
 
 }  // namespace
@@ -454,10 +487,10 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 t.cond = 0xffff;
                 t.first = (uint16_t)nmat;
                 t.count = (uint16_t)(j - i);
-                // matrices stored in register-bit order
+                // rotation forms (c, s, phase turns a, p, l) in register-bit order
                 for (int b = 0; b < 5; ++b)
                     for (int q = i; q < j; ++q)
-                        if (out[q].k == b) std::memcpy(P.mats[nmat++], out[q].m, sizeof(float) * 8);
+                        if (out[q].k == b) rotation_form(out[q].m, P.mats[nmat++]);
                 i = j;
             }
             if (overflow) {

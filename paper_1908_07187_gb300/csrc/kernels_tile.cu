@@ -209,44 +209,31 @@ __device__ __forceinline__ void bit_factor_dispatch(int k, Regs &v, float2 f) {
     }
 }
 
-// Pending diagonal of one thread in 32-bit fixed-point turns.
+// Pending diagonal of one thread in 32-bit fixed-point turns.  The six sums live
+// in shared memory (word w of thread x at w * kTileThreads + x, conflict-free),
+// leaving the registers to the amplitudes; only the mask is a register.
 struct Pending {
-    uint32_t t0, t[5];
-    int mask;  // bit k: t[k] may be nonzero; bit 5: t0 may be nonzero
+    uint32_t *p;  // word 0: t0 (constant), word 1 + k: t_k (register bit k)
+    float2 *fa;   // flush scratch: factor k at fa[k * kTileThreads]
+    int mask;     // bit k: t_k may be nonzero; bit 5: t0 may be nonzero
 
+    __device__ __forceinline__ uint32_t &t0() { return p[0]; }
+    __device__ __forceinline__ uint32_t &t(int k) { return p[(k + 1) * kTileThreads]; }
     __device__ __forceinline__ void reset() {
-        t0 = 0;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) t[k] = 0;
+        for (int w = 0; w < 6; ++w) p[w * kTileThreads] = 0;
         mask = 0;
     }
-    __device__ __forceinline__ uint32_t get(int k) const {
-        switch (k) {
-            case 0: return t[0];
-            case 1: return t[1];
-            case 2: return t[2];
-            case 3: return t[3];
-            default: return t[4];
-        }
-    }
     __device__ __forceinline__ void add(int k, uint32_t d) {
-        switch (k) {
-            case 0: t[0] += d; break;
-            case 1: t[1] += d; break;
-            case 2: t[2] += d; break;
-            case 3: t[3] += d; break;
-            default: t[4] += d; break;
-        }
+        t(k) += d;
         mask |= 1 << k;
     }
+    __device__ __forceinline__ void add0(uint32_t d) {
+        t0() += d;
+        mask |= 32;
+    }
     __device__ __forceinline__ void clear(int k) {
-        switch (k) {
-            case 0: t[0] = 0; break;
-            case 1: t[1] = 0; break;
-            case 2: t[2] = 0; break;
-            case 3: t[3] = 0; break;
-            default: t[4] = 0; break;
-        }
+        t(k) = 0;
         mask &= ~(1 << k);
     }
     __device__ __forceinline__ void flush(Regs &v) {
@@ -254,14 +241,20 @@ struct Pending {
         if ((mask & 32) == 0 && __popc(mask) <= 2) {
 #pragma unroll
             for (int k = 0; k < 5; ++k)
-                if ((mask & (1 << k)) && t[k] != 0) bit_factor_dispatch(k, v, turns_to_phase(t[k]));
+                if (mask & (1 << k)) {
+                    const uint32_t tk = t(k);
+                    if (tk != 0) bit_factor_dispatch(k, v, turns_to_phase(tk));
+                }
         } else {
-            // D(r) = c0 * prod_{k in r} a_k: six sincos, then walk j (register
-            // bits 1..4) in Gray-code order so D changes by one factor per step
-            const float2 c0 = (mask & 32) ? turns_to_phase(t0) : make_float2(1.f, 0.f);
-            float2 a[5];
+            // D(r) = c0 * prod_{k in r} a_k: six sincos into this thread's factor
+            // slots in shared memory (not registers: the amplitudes fill those), then
+            // walk j (register bits 1..4) in Gray-code order so D changes by one factor
+            // per step
+            const float2 c0 = (mask & 32) ? turns_to_phase(t0()) : make_float2(1.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) a[k] = (mask & (1 << k)) ? turns_to_phase(t[k]) : make_float2(1.f, 0.f);
+            for (int k = 0; k < 5; ++k)
+                fa[k * kTileThreads] = (mask & (1 << k)) ? turns_to_phase(t(k)) : make_float2(1.f, 0.f);
+            const float2 a0 = fa[0];
             float2 d = c0;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
@@ -269,9 +262,10 @@ struct Pending {
                 if (i > 0) {
                     const int gp = (i - 1) ^ ((i - 1) >> 1);
                     const int b = ctz_const(g ^ gp);         // register bit b + 1 toggles
-                    d = cmul(d, (g >> b) & 1 ? a[b + 1] : make_float2(a[b + 1].x, -a[b + 1].y));
+                    const float2 ab = fa[(b + 1) * kTileThreads];
+                    d = cmul(d, (g >> b) & 1 ? ab : make_float2(ab.x, -ab.y));
                 }
-                const float2 d1 = cmul(d, a[0]);
+                const float2 d1 = cmul(d, a0);
                 const float2 Dr = make_float2(d.x, d1.x), Di = make_float2(d.y, d1.y);
                 const float2 A = v.R[g], B = v.I[g];
                 v.R[g] = __ffma2_rn(make_float2(-Di.x, -Di.y), B, __fmul2_rn(Dr, A));
@@ -329,7 +323,7 @@ __device__ __forceinline__ void layer_gate(Regs &v, Pending &pd, const float *m)
     const float c = m[0], s = m[1];
     const uint32_t ta = __float_as_uint(m[2]), tp = __float_as_uint(m[3]);
     uint32_t tb = __float_as_uint(m[4]);
-    if (pd.mask & (1 << K)) tb += pd.t[K];
+    if (pd.mask & (1 << K)) tb += pd.t(K);
     float2 m01 = make_float2(-s, 0.f), m11 = make_float2(c, 0.f);
     if (tb != 0) {
         const float2 b = turns_to_phase(tb);
@@ -337,13 +331,10 @@ __device__ __forceinline__ void layer_gate(Regs &v, Pending &pd, const float *m)
         m11 = make_float2(c * b.x, c * b.y);
     }
     rot_butterfly<K>(v, c, s, m01, m11);
-    pd.t[K] = tp;
+    pd.t(K) = tp;
     if (tp != 0) pd.mask |= 1 << K;
     else pd.mask &= ~(1 << K);
-    if (ta != 0) {
-        pd.t0 += ta;
-        pd.mask |= 32;
-    }
+    if (ta != 0) pd.add0(ta);
 }
 
 // amplitudes whose register bits K and L are both 1 are multiplied by f (or negated)
@@ -371,9 +362,17 @@ __device__ __forceinline__ void pair_factor(Regs &v, float2 f, bool neg) {
     pair_all<K, L>(v, f, neg, std::make_integer_sequence<int, 32>{});
 }
 
-__device__ __forceinline__ bool op_applies(const TileOp &op, int tbits, uint64_t base, unsigned condok) {
+// fixed-bit masks and the tile base in the offset width (32 bits while n <= 32)
+template <typename Off>
+__device__ __forceinline__ Off ld_mask(const uint64_t *p) {
+    if constexpr (sizeof(Off) == 4) return __ldg(reinterpret_cast<const uint32_t *>(p));  // low word
+    else return __ldg(reinterpret_cast<const unsigned long long *>(p));
+}
+
+template <typename Off>
+__device__ __forceinline__ bool op_applies(const TileOp &op, int tbits, Off base, unsigned condok) {
     if ((tbits & op.tmask) != op.tval) return false;
-    if ((base & op.gmask) != op.gval) return false;
+    if ((base & (Off)op.gmask) != (Off)op.gval) return false;
     if (op.cond != 0xffff && !((condok >> op.cond) & 1u)) return false;
     return true;
 }
@@ -408,9 +407,16 @@ __device__ __forceinline__ void store_all(float2 *dst, const Offsets<Off> &o, Re
 
 template <typename Off>
 __global__ void __launch_bounds__(kTileThreads, 2)
-    k_tile(float2 *__restrict__ psi, const __grid_constant__ TileParams P, const uint8_t *__restrict__ cbits) {
-    extern __shared__ __align__(16) float smf[];   // 2 x 2^13 floats (64 KiB)
+    k_tile(float2 *__restrict__ psi, const __grid_constant__ TileParams P, const TileEntries *__restrict__ tab,
+           const uint8_t *__restrict__ cbits) {
+    // 2 x 2^13 floats (64 KiB) for transposes, then per thread five flush factors, six
+    // pending words and one word per TOP_PHASES op
+    extern __shared__ __align__(16) float smf[];
     float *sre = smf, *sim = smf + (1 << kTileQubits);
+    float2 *sfa = reinterpret_cast<float2 *>(smf + (2 << kTileQubits));       // flush factors
+    uint32_t *spd = reinterpret_cast<uint32_t *>(sfa + 5 * kTileThreads);       // pending sums
+    uint32_t *sph = spd + 6 * kTileThreads;                                      // phase-op sums
+    uint32_t *spat = sph + P.nphops * kTileThreads;                              // pattern sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tbits = (warp << 5) | lane;
 
@@ -422,13 +428,14 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     }
 
     for (uint64_t tile = blockIdx.x; tile < P.n_tiles; tile += gridDim.x) {
-        uint64_t base = 0;
-        for (int b = 0; b < P.nfix; ++b) base |= ((tile >> b) & 1ull) << P.fixed[b];
+        uint64_t base64 = 0;
+        for (int b = 0; b < P.nfix; ++b) base64 |= ((tile >> b) & 1ull) << P.fixed[b];
+        const Off base = (Off)base64;
 
         // load in ARR_IO: lanes = local 0..4, registers = local 5..9, warps = local 10..12
         Regs v;
         {
-            uint64_t tb = base + (uint64_t)lane;
+            uint64_t tb = (uint64_t)base + (uint64_t)lane;
 #pragma unroll
             for (int j = 0; j < 3; ++j)
                 if ((warp >> j) & 1) tb += 1ull << P.S[10 + j];
@@ -437,7 +444,36 @@ __global__ void __launch_bounds__(kTileThreads, 2)
             load_all<Off>(psi + tb, o, v, std::make_integer_sequence<int, 32>{});
         }
 
+        // the pass's phase sums for this tile and thread, while the loads are in flight:
+        // one thread per pattern adds its fixed-bit-conditioned terms (uniform over the
+        // tile), then every thread adds the patterns whose thread-bit condition it meets
+        if (P.nphops) {
+            for (int q = threadIdx.x; q < P.npats; q += kTileThreads) {
+                const PhasePattern pt = tab->p[q];
+                uint32_t sum = pt.turns;
+                const int ende = pt.first + pt.count;
+                for (int e = pt.first; e < ende; ++e) {
+                    const Off gm = ld_mask<Off>(&tab->e[e].gmask), gv = ld_mask<Off>(&tab->e[e].gval);
+                    const uint32_t tu = __ldg(&tab->e[e].turns);
+                    sum += ((base & gm) == gv) ? tu : 0u;
+                }
+                spat[q] = sum;
+            }
+            __syncthreads();
+            for (int slot = 0; slot < P.nphops; ++slot) {
+                uint32_t acc = 0;
+                const int endp = P.phop[slot][0] + P.phop[slot][1];
+                for (int q = P.phop[slot][0]; q < endp; ++q) {
+                    const PhasePattern &pt = P.pats[q];
+                    acc += ((tbits & pt.tmask) == pt.tval) ? spat[q] : 0u;
+                }
+                sph[slot * kTileThreads + threadIdx.x] = acc;
+            }
+        }
+
         Pending pd;
+        pd.p = spd + threadIdx.x;
+        pd.fa = sfa + threadIdx.x;
         pd.reset();
         int cur = ARR_IO;
         for (int i = 0; i < P.nops; ++i) {
@@ -459,30 +495,15 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                 continue;
             }
             if (op.kind == TOP_PHASES) {
-                // tile-uniform terms: the 32 lanes share them out, then an integer sum
-                uint32_t acc = 0;
-                const int endu = op.first + op.count;
-                for (int e = op.first + lane; e < endu; e += 32) {
-                    const PhaseEntry &pe = P.entries[e];
-                    acc += ((base & pe.gmask) == pe.gval) ? pe.turns : 0u;
-                }
-                if (op.count) acc = __reduce_add_sync(0xffffffffu, acc);
-                // terms that depend on the thread: each thread sums its own
-                const int endt = endu + op.count2;
-                for (int e = endu; e < endt; ++e) {
-                    const PhaseEntry &pe = P.entries[e];
-                    const bool on = ((tbits & pe.tmask) == pe.tval) & ((base & pe.gmask) == pe.gval);
-                    acc += on ? pe.turns : 0u;
-                }
+                const uint32_t acc = sph[op.count2 * kTileThreads + threadIdx.x];
                 if (op.k == 5) {
-                    pd.t0 += acc;
-                    pd.mask |= 32;
+                    pd.add0(acc);
                 } else {
                     pd.add(op.k, acc);
                 }
                 continue;
             }
-            if (!op_applies(op, tbits, base, condok)) continue;
+            if (!op_applies<Off>(op, tbits, base, condok)) continue;
             if (op.kind == TOP_PAIR) {
                 const float2 f = make_float2(op.ph.re, op.ph.im);
                 const bool neg = op.ph.turns == 0x80000000u;
@@ -505,7 +526,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                 float2 m10 = make_float2(op.m[4], op.m[5]), m11 = make_float2(op.m[6], op.m[7]);
                 const int k = op.k;
                 if (pd.mask & (1 << k)) {
-                    const uint32_t tk = pd.get(k);
+                    const uint32_t tk = pd.t(k);
                     if (tk != 0) {
                         const float2 ak = turns_to_phase(tk);
                         if (op.rmask == 0) {  // fold diag(1, a_k) into the gate: U * diag(1, a_k)
@@ -532,15 +553,13 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                 const int rm = op.rmask;
                 const int pc = __popc(rm);
                 if (pc == 0) {
-                    pd.t0 += op.ph.turns;
-                    pd.mask |= 32;
+                    pd.add0(op.ph.turns);
                 } else if (pc == 1) {
                     const int k = __ffs(rm) - 1;
                     if (op.rval) {
                         pd.add(k, op.ph.turns);
                     } else {  // f on bit k = 0:  f * (f^-1 on bit k = 1)
-                        pd.t0 += op.ph.turns;
-                        pd.mask |= 32;
+                        pd.add0(op.ph.turns);
                         pd.add(k, 0u - op.ph.turns);
                     }
                 } else {
@@ -566,7 +585,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
 
         // store in ARR_IO or ARR_HI (lanes = local 0..4 in both)
         {
-            uint64_t tb = base + (uint64_t)lane;
+            uint64_t tb = (uint64_t)base + (uint64_t)lane;
             Offsets<Off> o;
             if (cur == ARR_IO) {
 #pragma unroll
@@ -585,27 +604,44 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     }
 }
 
+__global__ void k_tile_entries(const __grid_constant__ TileEntries E, int ne, int np, TileEntries *__restrict__ dst) {
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) dst->e[i] = E.e[i];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) dst->p[i] = E.p[i];
+}
+
 template <typename Off>
-cudaError_t launch_tile_t(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s) {
-    constexpr int smem = (int)(2 * sizeof(float)) << kTileQubits;
+cudaError_t launch_tile_t(void *psi, const TileParams &p, const TileEntries *entries, const uint8_t *cbits,
+                          cudaStream_t s) {
+    // transposes (2^13 complex64), flush factors (5 float2), pending (6 words), phase sums
+    constexpr int smem_max =
+        ((int)(2 * sizeof(float)) << kTileQubits) + (16 + kTileMaxPhOps) * kTileThreads * 4 + kTileMaxPats * 4;
+    const int smem = ((int)(2 * sizeof(float)) << kTileQubits) + (16 + p.nphops) * kTileThreads * 4 +
+                     (p.nphops ? p.npats * 4 : 0);
     static bool attr_set = false;  // the attribute is per function, once per process
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile<Off>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_tile<Off>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     uint64_t grid = p.n_tiles;
     if (grid > (1ull << 30)) grid = 1ull << 30;
-    k_tile<Off><<<(unsigned)grid, kTileThreads, smem, s>>>((float2 *)psi, p, cbits);
+    k_tile<Off><<<(unsigned)grid, kTileThreads, smem, s>>>((float2 *)psi, p, entries, cbits);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_tile(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s) {
+cudaError_t launch_tile(void *psi, const TileParams &p, const TileEntries *entries, const uint8_t *cbits,
+                        cudaStream_t s) {
     // 32-bit element offsets inside a tile reach 2^32 amplitudes
-    if (p.n <= 32) return launch_tile_t<uint32_t>(psi, p, cbits, s);
-    return launch_tile_t<uint64_t>(psi, p, cbits, s);
+    if (p.n <= 32) return launch_tile_t<uint32_t>(psi, p, entries, cbits, s);
+    return launch_tile_t<uint64_t>(psi, p, entries, cbits, s);
+}
+
+cudaError_t launch_tile_entries(const TileEntries &e, int nentries, int npats, TileEntries *dst, cudaStream_t s) {
+    if (nentries <= 0 && npats <= 0) return cudaSuccess;
+    k_tile_entries<<<1, 256, 0, s>>>(e, nentries, npats, dst);
+    return cudaGetLastError();
 }
 
 }  // namespace qk

@@ -129,22 +129,42 @@ constexpr int kTileQubits = 13;
 constexpr int kTileThreads = 256;
 constexpr int kTileMaxOps = 192;
 constexpr int kTileMaxEntries = 512;
+constexpr int kTileMaxPats = 320;
 constexpr int kTileMaxMats = 160;
 constexpr int kTileMaxConds = 4;
+constexpr int kTileMaxPhOps = 24;   // TOP_PHASES ops per pass (their sums live in shared memory)
 enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
 // TOP_PHASES: a group of diagonal terms that all add to one pending phase sum
-// (register bit k, or the constant when k == 5); each entry adds its turns when
-// its thread-bit and fixed-bit conditions hold.
+// (register bit k, or the constant when k == 5), as patterns [first, first +
+// count): each pattern is the terms sharing one thread-bit condition; its
+// fixed-bit-conditioned terms are entries in global memory, summed by the lanes
+// of a warp in parallel (the condition is uniform over a tile).  The sums do not
+// depend on the amplitudes, so every TOP_PHASES op of a pass is summed when a
+// tile starts and kept in shared memory (slot count2) until the op runs.
 // TOP_U2L: a layer of uncontrolled 2x2 gates on distinct register bits (k is
 // the bit mask); their matrices are mats[first...] in bit order.
 // TOP_PAIR: factor on the amplitudes whose register bits k and l are both 1
 // (code k | l << 3), under the op's thread / fixed-bit conditions.
 enum TileOpKind : uint8_t { TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_PHASES = 3, TOP_U2L = 4, TOP_PAIR = 5 };
 
+// A diagonal term conditioned on fixed (non-tile) bits: adds turns when
+// (tile base & gmask) == gval.
 struct PhaseEntry {
-    uint16_t tmask, tval;
-    uint32_t turns;
     uint64_t gmask, gval;
+    uint32_t turns, pad;
+};
+// The terms of one TOP_PHASES group that share a thread-bit condition.
+struct PhasePattern {
+    uint16_t tmask, tval;
+    uint16_t first, count;  // entries [first, first + count)
+    uint32_t turns;         // sum of the terms without a fixed-bit condition
+};
+// A pass's entries and patterns, copied to a device buffer by a one-block kernel
+// before the tile kernel runs (kernel parameters serve a warp well only at
+// uniform addresses; the tile kernel reads these at per-thread addresses).
+struct TileEntries {
+    PhaseEntry e[kTileMaxEntries];
+    PhasePattern p[kTileMaxPats];
 };
 
 struct TileOp {
@@ -153,8 +173,8 @@ struct TileOp {
     uint8_t rmask, rval;   // condition on register bits (5-bit register index space)
     uint16_t tmask, tval;  // condition on thread bits: bits 0..4 lane, 5..7 warp
     uint16_t cond;         // index into TileParams::conds, 0xffff = unconditional
-    uint16_t count;        // TOP_PHASES: tile-uniform entries [first, first + count), then
-    uint16_t first;        //   count2 thread-dependent entries
+    uint16_t count;        // TOP_PHASES: patterns [first, first + count); TOP_U2L: gates
+    uint16_t first;        //   from mats[first]
     uint16_t count2;
     uint64_t gmask, gval;  // condition on the tile's fixed (non-tile) physical bits
     union {
@@ -177,13 +197,18 @@ struct TileParams {
     Cond conds[kTileMaxConds];
     int nops;
     int nentries;
+    int npats;
+    int nphops;                             // TOP_PHASES ops; op.count2 is the op's slot
+    uint16_t phop[kTileMaxPhOps][2];        // slot -> (first pattern, pattern count)
     TileOp ops[kTileMaxOps];
-    PhaseEntry entries[kTileMaxEntries];
+    PhasePattern pats[kTileMaxPats];
     float mats[kTileMaxMats][8];
 };
 static_assert(sizeof(TileParams) <= 32764, "tile program must fit in the kernel parameter space");
 
-cudaError_t launch_tile(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s);
+cudaError_t launch_tile(void *psi, const TileParams &p, const TileEntries *entries, const uint8_t *cbits,
+                        cudaStream_t s);
+cudaError_t launch_tile_entries(const TileEntries &e, int nentries, int npats, TileEntries *dst, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // launchers (kernels_basic.cu); prec: 0 = complex64, 1 = complex128

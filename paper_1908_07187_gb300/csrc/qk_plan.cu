@@ -220,6 +220,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             }
 
         static thread_local TileParams P;
+        static thread_local TileEntries E;
         std::memset(&P, 0, offsetof(TileParams, ops));
         P.n = n;
         P.n_tiles = 1ull << (n - kTileQubits);
@@ -325,7 +326,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
         // group runs of consecutive diagonal terms by the pending sum they feed
         {
             static thread_local TileOp out[2 * kTileMaxOps + 8];
-            int nout = 0, nent = 0;
+            int nout = 0, nent = 0, npat = 0, nph = 0;
             bool overflow = false;
             for (int i = 0; i < nops && !overflow;) {
                 if (nout >= 2 * kTileMaxOps) {
@@ -339,7 +340,12 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 int j = i;
                 while (j < nops && prog[j].kind == TOP_PHASE) ++j;
                 // per pending sum (register bit 0..4, constant 5): entries that add turns
-                std::vector<PhaseEntry> grp[6];
+                struct Term {
+                    uint16_t tmask, tval;
+                    uint32_t turns;
+                    uint64_t gmask, gval;
+                };
+                std::vector<Term> grp[6];
                 // terms on two register bits, reduced to the (1,1) pattern: key -> turns
                 struct PairKey {
                     int code;
@@ -349,7 +355,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 };
                 std::vector<PairKey> pairs;
                 auto add_entry = [&](int g, const TileOp &o, uint32_t turns) {
-                    PhaseEntry e;
+                    Term e;
                     e.tmask = o.tmask;
                     e.tval = o.tval;
                     e.gmask = o.gmask;
@@ -430,24 +436,63 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 }
                 for (int g = 0; g < 6 && !overflow; ++g) {
                     if (grp[g].empty()) continue;
-                    if (nent + (int)grp[g].size() > kTileMaxEntries || nout >= 2 * kTileMaxOps) {
-                        overflow = true;
-                        break;
+                    // patterns: the group's terms by thread-bit condition; within one,
+                    // terms with equal fixed-bit conditions merge, and those with none
+                    // become the pattern's constant
+                    std::sort(grp[g].begin(), grp[g].end(), [](const Term &a, const Term &b) {
+                        if (a.tmask != b.tmask) return a.tmask < b.tmask;
+                        if (a.tval != b.tval) return a.tval < b.tval;
+                        if (a.gmask != b.gmask) return a.gmask < b.gmask;
+                        return a.gval < b.gval;
+                    });
+                    const int pat0 = npat;
+                    for (size_t a = 0; a < grp[g].size() && !overflow;) {
+                        size_t b = a;
+                        while (b < grp[g].size() && grp[g][b].tmask == grp[g][a].tmask &&
+                               grp[g][b].tval == grp[g][a].tval)
+                            ++b;
+                        PhasePattern pt{};
+                        pt.tmask = grp[g][a].tmask;
+                        pt.tval = grp[g][a].tval;
+                        pt.first = (uint16_t)nent;
+                        for (size_t x = a; x < b;) {
+                            size_t y = x;
+                            uint32_t tu = 0;
+                            while (y < b && grp[g][y].gmask == grp[g][x].gmask && grp[g][y].gval == grp[g][x].gval)
+                                tu += grp[g][y++].turns;
+                            if (grp[g][x].gmask == 0) {
+                                pt.turns += tu;
+                            } else if (tu != 0) {
+                                if (nent >= kTileMaxEntries) { overflow = true; break; }
+                                PhaseEntry &e = E.e[nent++];
+                                e.gmask = grp[g][x].gmask;
+                                e.gval = grp[g][x].gval;
+                                e.turns = tu;
+                                e.pad = 0;
+                            }
+                            x = y;
+                        }
+                        pt.count = (uint16_t)(nent - pt.first);
+                        if (!overflow && (pt.count || pt.turns)) {
+                            if (npat >= kTileMaxPats) { overflow = true; break; }
+                            E.p[npat] = pt;
+                            P.pats[npat++] = pt;
+                        }
+                        a = b;
                     }
+                    if (overflow || npat == pat0) continue;
+                    if (nout >= 2 * kTileMaxOps || nph >= kTileMaxPhOps) { overflow = true; break; }
                     TileOp &t = out[nout++];
                     std::memset(&t, 0, sizeof t);
                     t.kind = TOP_PHASES;
                     t.k = (uint8_t)g;
                     t.cond = 0xffff;
-                    t.first = (uint16_t)nent;
-                    // tile-uniform entries first (no thread-bit condition), then the rest
-                    int nu = 0;
-                    for (const auto &e : grp[g])
-                        if (e.tmask == 0) { P.entries[nent++] = e; ++nu; }
-                    for (const auto &e : grp[g])
-                        if (e.tmask != 0) P.entries[nent++] = e;
-                    t.count = (uint16_t)nu;
-                    t.count2 = (uint16_t)(grp[g].size() - nu);
+                    t.first = (uint16_t)pat0;
+                    t.count = (uint16_t)(npat - pat0);
+                    t.count2 = (uint16_t)nph;
+                    P.phop[nph][0] = (uint16_t)pat0;
+                    P.phop[nph][1] = (uint16_t)(npat - pat0);
+                    ++nph;
                 }
                 i = j;
             }
@@ -501,6 +546,8 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             }
             nops = nfin;
             P.nentries = nent;
+            P.npats = npat;
+            P.nphops = nph;
         }
         P.nops = nops;
         P.store_arr = cur;
@@ -521,8 +568,14 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             cudaEventCreate(&ev1);
             cudaEventRecord(ev0, ctx_stream(c));
         }
+        if (P.nphops > 0) {
+            ctx_launch_begin(c, 6, 2.0 * (sizeof(PhaseEntry) * P.nentries + sizeof(PhasePattern) * P.npats), &tok);
+            cudaError_t e = launch_tile_entries(E, P.nentries, P.npats, ctx_tile_entries(c), ctx_stream(c));
+            ctx_launch_end(tok);
+            if (e != cudaSuccess) return ctx_fail(c, QK_ECUDA, cudaGetErrorString(e));
+        }
         ctx_launch_begin(c, 0, 2.0 * 8.0 * (double)(1ull << n), &tok);
-        cudaError_t e = launch_tile(ctx_state(c), P, ctx_cbits(c), ctx_stream(c));
+        cudaError_t e = launch_tile(ctx_state(c), P, ctx_tile_entries(c), ctx_cbits(c), ctx_stream(c));
         ctx_launch_end(tok);
         if (e != cudaSuccess) return ctx_fail(c, QK_ECUDA, cudaGetErrorString(e));
         if (planner->log) {

@@ -37,6 +37,7 @@ int ctx_sms(qk_ctx *c);
 int ctx_tile_qubits(qk_ctx *c);
 cudaStream_t ctx_stream(qk_ctx *c);
 const uint8_t *ctx_cbits(qk_ctx *c);
+TileEntries *ctx_tile_entries(qk_ctx *c);   // device copy of a pass's phase entries and patterns
 qk_status ctx_run_plain(qk_ctx *c, const FusedOp &op);
 qk_status ctx_fail(qk_ctx *c, qk_status s, const char *msg);
 void ctx_launch_begin(qk_ctx *c, int cls, double bytes, void **token);

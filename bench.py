@@ -37,6 +37,24 @@ UNIT = "gates/s"
 FALLBACK_HBM_GBS = 6800.0
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks (the whole job is as
+    slow as its slowest replica); the values themselves on one rank."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(units_per_step: int, steps: int, world: int, seconds: float) -> float:
+    """Units processed by all ranks (each rank runs its own replica of the step)
+    divided by the slowest rank's time."""
+    return world * units_per_step * steps / seconds
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -429,11 +447,9 @@ def main():
     prof = ctx.profile()
     if dist:
         dist.barrier()
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks([ms], dist, "cuda")[0]
     ms_per_step = ms / args.steps
-    value = world * n_gates * args.steps / (ms / 1000.0)
+    value = job_throughput(n_gates, args.steps, world, ms / 1000.0)
 
     # end to end through the public API: host gate descriptors in, outcome out
     h2d = 0
@@ -444,14 +460,16 @@ def main():
     d2h = 8
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx.reset()
         qk.run_ops(ctx, gops)
         for op in meas:
             outcome = ctx.measure(op.targets, op.uniforms, op.cbits, wait=True)
-    t_e2e = time.perf_counter() - t0
-    e2e_value = world * n_gates * e2e_steps / t_e2e
+    t_e2e = max_over_ranks([time.perf_counter() - t0], dist, "cuda")[0]
+    e2e_value = job_throughput(n_gates, e2e_steps, world, t_e2e)
     _ = outcome
 
     # one-pass-per-gate comparison (fused vs plain), a short run

@@ -215,16 +215,24 @@ __global__ void __launch_bounds__(kThreads) k_perm(const typename Amp<R>::T *__r
         uint64_t src = i;
         if (active && (i & a.cmask) == a.cmask) {
             uint64_t y = 0;
-            for (int b = 0; b < a.w; ++b) y = (y << 1) | ((i >> a.rpos[b]) & 1u);
+            if (a.field.contig) {
+                y = field_get(i, a.field, a.w);
+            } else {
+                for (int b = 0; b < a.w; ++b) y = (y << 1) | ((i >> a.rpos[b]) & 1u);
+            }
             uint64_t x = y;
             if (a.kind == 0) {
                 if (y < a.N) x = mulmod_barrett(a.cinv, y, a.N, a.mu);
             } else {
                 x = a.finv[y];
             }
-            for (int b = 0; b < a.w; ++b) {
-                const uint64_t bit = (x >> (a.w - 1 - b)) & 1u;
-                src = (src & ~(1ull << a.rpos[b])) | (bit << a.rpos[b]);
+            if (a.field.contig) {
+                src = field_put(src, x, a.field, a.w);
+            } else {
+                for (int b = 0; b < a.w; ++b) {
+                    const uint64_t bit = (x >> (a.w - 1 - b)) & 1u;
+                    src = (src & ~(1ull << a.rpos[b])) | (bit << a.rpos[b]);
+                }
             }
         }
         out[i] = in[src];

@@ -41,13 +41,18 @@ __device__ __forceinline__ uint64_t mulmod_barrett(uint64_t x, uint64_t y, uint6
 // index of the amplitude whose register value is f^-1(register value of i)
 __device__ __forceinline__ uint64_t source_index(uint64_t i, const KitaevArgs &a) {
     uint64_t y = 0;
-    for (int b = 0; b < a.w; ++b) y = (y << 1) | ((i >> a.rpos[b]) & 1u);
+    if (a.field.contig) {
+        y = field_get(i, a.field, a.w);
+    } else {
+        for (int b = 0; b < a.w; ++b) y = (y << 1) | ((i >> a.rpos[b]) & 1u);
+    }
     uint64_t x = y;
     if (a.kind == 0) {
         if (y < a.N) x = mulmod_barrett(a.cinv, y, a.N, a.mu);
     } else {
         x = a.finv[y];
     }
+    if (a.field.contig) return field_put(i, x, a.field, a.w);
     uint64_t src = i;
     for (int b = 0; b < a.w; ++b) {
         const uint64_t bit = (x >> (a.w - 1 - b)) & 1u;

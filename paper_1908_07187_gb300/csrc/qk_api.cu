@@ -765,6 +765,7 @@ qk_status qk_apply_gate(qk_ctx *c, int gate_id, const int *targets, int nt, cons
     qk::PermArgs a{};
     a.w = g.k;
     for (int t = 0; t < g.k; ++t) a.rpos[t] = c->l2p[targets[t]];
+    a.field = qk::reg_field_of(a.rpos, g.k);
     a.cmask = cmask;
     a.n_amps = 1ull << c->n;
     a.kind = g.kind == 1 ? 0 : 1;
@@ -834,6 +835,7 @@ qk_status qk_apply_kitaev_stage(qk_ctx *c, int control, int gate_id, const int *
     a.cpos = c->l2p[control];
     a.w = g.k;
     for (int t = 0; t < g.k; ++t) a.rpos[t] = c->l2p[targets[t]];
+    a.field = qk::reg_field_of(a.rpos, g.k);
     a.kind = g.kind == 1 ? 0 : 1;
     a.N = g.N;
     a.cinv = g.cinv;

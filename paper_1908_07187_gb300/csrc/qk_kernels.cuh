@@ -60,9 +60,40 @@ struct MatKArgs {
 };
 
 // Controlled permutation of a w-bit register, out-of-place gather.
+// A register whose qubits sit on consecutive physical bits p0 .. p0 + w - 1 is a bit
+// field of the index: its value is the field itself (first-listed qubit highest,
+// rev = 0) or the field bit-reversed (first-listed qubit lowest, rev = 1).  Kernels
+// use the field form when contig is set and the per-bit gather otherwise.
+struct RegField {
+    int contig, p0, rev;
+};
+inline RegField reg_field_of(const int *rpos, int w) {
+    RegField f{0, 0, 0};
+    bool asc = true, desc = true;
+    for (int t = 0; t < w; ++t) {
+        asc = asc && rpos[t] == rpos[0] + t;
+        desc = desc && rpos[t] == rpos[0] - t;
+    }
+    if (w >= 1 && asc) f = RegField{1, rpos[0], 1};
+    else if (w >= 1 && desc) f = RegField{1, rpos[w - 1], 0};
+    return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ uint64_t field_get(uint64_t i, const RegField &f, int w) {
+    const uint64_t v = (i >> f.p0) & ((1ull << w) - 1);
+    return f.rev ? (__brevll(v) >> (64 - w)) : v;
+}
+__device__ __forceinline__ uint64_t field_put(uint64_t i, uint64_t x, const RegField &f, int w) {
+    const uint64_t v = f.rev ? (__brevll(x) >> (64 - w)) : x;
+    const uint64_t m = ((1ull << w) - 1) << f.p0;
+    return (i & ~m) | (v << f.p0);
+}
+#endif
+
 struct PermArgs {
     int w;
     int rpos[kMaxPermW];  // physical bit of register list entry a (a = 0 is the MSB)
+    RegField field;       // zero (per-bit gather) unless set from rpos
     uint64_t cmask;
     uint64_t n_amps;
     int kind;             // 0 = mul-mod, 1 = table
@@ -98,6 +129,7 @@ struct KitaevArgs {
     int cpos;
     int w;
     int rpos[kMaxPermW];
+    RegField field;
     int kind;             // 0 = mul-mod, 1 = table
     uint64_t N, cinv, mu;
     const uint32_t *finv;

@@ -162,6 +162,28 @@ def test_mulmod_permutation_bit_exact(qk, prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("reg", [list(range(4, 12)), list(range(11, 3, -1)), [0, 1, 2, 3, 4, 5, 6, 7]])
+def test_mulmod_on_contiguous_registers_bit_exact(qk, reg):
+    # registers on consecutive physical bits take the bit-field index path
+    # (first-listed qubit lowest: bit-reversed field; highest: the field itself)
+    n = 13
+    N, c = 211, 37
+    psi = workloads.random_state(n, 16)
+    ctx = new_ctx(qk, n, "c64", "fused", psi)
+    gid = ctx.define_gate_perm_mulmod(8, c, N)
+    ctrl = 12 if 12 not in reg else 3
+    ctx.apply_gate(gid, reg, [ctrl])
+    ref = oracle.OracleState(n, psi=psi.astype(np.complex64))
+    ref.apply_mulmod(c, N, reg, [ctrl])
+    assert np.array_equal(ctx.get_state(), ref.psi)
+    f = np.random.default_rng(4).permutation(256).astype(np.uint64)
+    tid = ctx.define_gate_perm_table(f)
+    ctx.apply_gate(tid, reg)
+    ref.apply_perm(f, reg)
+    assert np.array_equal(ctx.get_state(), ref.psi)
+    ctx.close()
+
+
 def test_perm_table_and_rejections(qk):
     n = 6
     rng = np.random.default_rng(3)

@@ -134,7 +134,13 @@ template <typename R, int V>
 __global__ void __launch_bounds__(kThreads) k_phase(typename Amp<R>::T *psi, PhaseArgs a, const uint8_t *cbits) {
     using T = typename Amp<R>::T;
     if (a.cond.n && !cond_ok(a.cond, cbits)) return;
-    const T f = phase_factor<R>(a, cbits);
+    // an angle from cbits is formed in FP64 once per block (GB300's FP64 rate is low)
+    __shared__ T s_f;
+    if (a.n_rphase) {
+        if (threadIdx.x == 0) s_f = phase_factor<R>(a, cbits);
+        __syncthreads();
+    }
+    const T f = a.n_rphase ? s_f : phase_factor<R>(a, cbits);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < a.n_units; u += stride) {
         if constexpr (V == 1) {

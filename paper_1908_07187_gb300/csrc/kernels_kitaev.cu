@@ -71,6 +71,15 @@ __device__ __forceinline__ double2 rphase(const KitaevArgs &a, const uint8_t *cb
     return make_double2(c, s);
 }
 
+// the stage's phase factor, formed in FP64 by one thread per block (GB300's FP64
+// rate is low) and shared
+__device__ __forceinline__ double2 block_rphase(const KitaevArgs &a, const uint8_t *cbits) {
+    __shared__ double2 s_om;
+    if (threadIdx.x == 0) s_om = rphase(a, cbits);
+    __syncthreads();
+    return s_om;
+}
+
 __device__ __forceinline__ double block_sum(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -87,7 +96,7 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads) k_kitaev_reduce(const typename Amp<R>::T *__restrict__ psi, KitaevArgs a,
                                                             const uint8_t *cbits, double *partials) {
     __shared__ double sh[kThreads / 32];
-    const double2 om = rphase(a, cbits);
+    const double2 om = block_rphase(a, cbits);
     const R wr = (R)om.x, wi = (R)om.y;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     double d0 = 0.0, d1 = 0.0;
@@ -120,7 +129,7 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads) k_kitaev_update(const typename Amp<R>::T *__restrict__ psi,
                                                             typename Amp<R>::T *__restrict__ out, KitaevArgs a,
                                                             const uint8_t *cbits, const MeasSlot *slot) {
-    const double2 om = rphase(a, cbits);
+    const double2 om = block_rphase(a, cbits);
     const int m = slot->m;
     const R sc = (R)slot->scale;
     const R sg = m ? (R)-1 : (R)1;

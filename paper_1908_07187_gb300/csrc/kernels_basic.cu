@@ -282,7 +282,7 @@ __device__ __forceinline__ uint64_t insert_bits(uint64_t j, const MeasArgs &a) {
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_meas_reduce(const typename Amp<R>::T *__restrict__ psi, MeasArgs a,
-                                                          const MeasSlot *slots, double *partials) {
+                                                          const MeasSlot *slots, double *partials, Decide dec) {
     __shared__ double sh[kThreads / 32];
     const uint64_t pv = prefix_value(a, slots, a.k);
     const int q = a.pos[a.k];
@@ -329,28 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_meas_reduce(const typename Amp<R>:
         partials[2 * blockIdx.x] = s0;
         partials[2 * blockIdx.x + 1] = s1;
     }
-}
-
-__global__ void __launch_bounds__(kThreads) k_meas_decide(const double *partials, int nblocks, double u, MeasSlot *slot,
-                                                          uint8_t *cbits, int dest) {
-    __shared__ double sh[kThreads / 32];
-    double a0 = 0.0, a1 = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        a0 += partials[2 * b];
-        a1 += partials[2 * b + 1];
-    }
-    const double s0 = block_sum<double>(a0, sh);
-    const double s1 = block_sum<double>(a1, sh);
-    if (threadIdx.x == 0) {
-        const double tot = s0 + s1;
-        const double p0 = tot > 0.0 ? s0 / tot : 1.0;
-        const int m = (u >= p0) ? 1 : 0;
-        const double pm = m ? s1 : s0;
-        slot->p0 = p0;
-        slot->m = m;
-        slot->scale = pm > 0.0 ? 1.0 / sqrt(pm) : 0.0;
-        if (dest >= 0) cbits[dest] = (uint8_t)m;
-    }
+    last_block_decides(partials, dec);
 }
 
 // Project onto the decided outcomes of every measured qubit and renormalise:
@@ -484,18 +463,12 @@ cudaError_t launch_perm(int prec, const void *in, void *out, const PermArgs &a, 
 }
 
 cudaError_t launch_measure_reduce(int prec, const void *psi, int n, const MeasArgs &a, const MeasSlot *slots,
-                                  double *partials, int nblocks, cudaStream_t s) {
+                                  double *partials, int nblocks, const Decide &d, cudaStream_t s) {
     if (n < 1) return cudaErrorInvalidValue;
     if (prec == 0)
-        k_meas_reduce<float><<<nblocks, kThreads, 0, s>>>((const float2 *)psi, a, slots, partials);
+        k_meas_reduce<float><<<nblocks, kThreads, 0, s>>>((const float2 *)psi, a, slots, partials, d);
     else
-        k_meas_reduce<double><<<nblocks, kThreads, 0, s>>>((const double2 *)psi, a, slots, partials);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_measure_decide(const double *partials, int nblocks, double u, MeasSlot *slot,
-                                  uint8_t *cbits, int dest, cudaStream_t s) {
-    k_meas_decide<<<1, kThreads, 0, s>>>(partials, nblocks, u, slot, cbits, dest);
+        k_meas_reduce<double><<<nblocks, kThreads, 0, s>>>((const double2 *)psi, a, slots, partials, d);
     return cudaGetLastError();
 }
 

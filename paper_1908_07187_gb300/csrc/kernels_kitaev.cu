@@ -94,7 +94,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_kitaev_reduce(const typename Amp<R>::T *__restrict__ psi, KitaevArgs a,
-                                                            const uint8_t *cbits, double *partials) {
+                                                            const uint8_t *cbits, double *partials, Decide dec) {
     __shared__ double sh[kThreads / 32];
     const double2 om = block_rphase(a, cbits);
     const R wr = (R)om.x, wi = (R)om.y;
@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_kitaev_reduce(const typename Amp<R
         partials[2 * blockIdx.x] = s0;
         partials[2 * blockIdx.x + 1] = s1;
     }
+    last_block_decides(partials, dec);
 }
 
 template <typename R>
@@ -159,11 +160,11 @@ inline unsigned grid_for(uint64_t units, int sms) {
 }  // namespace
 
 cudaError_t launch_kitaev_reduce(int prec, const void *psi, const KitaevArgs &a, const uint8_t *cbits,
-                                 double *partials, int nblocks, cudaStream_t s) {
+                                 double *partials, int nblocks, const Decide &d, cudaStream_t s) {
     if (prec == 0)
-        k_kitaev_reduce<float><<<nblocks, kThreads, 0, s>>>((const float2 *)psi, a, cbits, partials);
+        k_kitaev_reduce<float><<<nblocks, kThreads, 0, s>>>((const float2 *)psi, a, cbits, partials, d);
     else
-        k_kitaev_reduce<double><<<nblocks, kThreads, 0, s>>>((const double2 *)psi, a, cbits, partials);
+        k_kitaev_reduce<double><<<nblocks, kThreads, 0, s>>>((const double2 *)psi, a, cbits, partials, d);
     return cudaGetLastError();
 }
 

@@ -64,6 +64,7 @@ struct qk_ctx {
 
     double *d_partials = nullptr;
     int *d_err = nullptr;          // set by a kernel whose bounded wait gave up
+    unsigned *d_counter = nullptr; // reduction ticket (zero between launches)
     int meas_blocks = 0;
     qk::MeasSlot *d_slots = nullptr;
     int slot_cap = 0;
@@ -481,6 +482,8 @@ qk_status qk_create(qk_ctx **out, qk_precision precision, void *cuda_stream, con
     c->meas_blocks = c->sms * kMeasBlocksPerSM;
     if (dalloc(c, (void **)&c->d_partials, sizeof(double) * 2 * c->meas_blocks) != cudaSuccess ||
         dalloc(c, (void **)&c->d_err, sizeof(int)) != cudaSuccess ||
+        dalloc(c, (void **)&c->d_counter, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
         dalloc(c, (void **)&c->d_tile_entries, sizeof(qk::TileEntries)) != cudaSuccess ||
         cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -505,6 +508,7 @@ qk_status qk_destroy(qk_ctx *c) {
         for (auto &e : g.tc_cache) dfree(c, e.second);
     }
     dfree(c, c->d_err);
+    dfree(c, c->d_counter);
     dfree(c, c->d_tile_entries);
     dfree(c, c->d_swap_mat);
     dfree(c, c->d_state);
@@ -847,13 +851,9 @@ qk_status qk_apply_kitaev_stage(qk_ctx *c, int control, int gate_id, const int *
     const double half = (double)c->amp * (double)a.n_half;
     {
         LaunchScope ls(c, 4, 2 * half);
-        CUDA_TRY(c, qk::launch_kitaev_reduce((int)c->prec, c->d_state, a, c->d_cbits, c->d_partials, c->meas_blocks,
+        const qk::Decide d{c->d_counter, uniform, c->d_slots, c->d_cbits, dest};
+        CUDA_TRY(c, qk::launch_kitaev_reduce((int)c->prec, c->d_state, a, c->d_cbits, c->d_partials, c->meas_blocks, d,
                                              c->stream));
-    }
-    {
-        LaunchScope ls(c, 6, 0);
-        CUDA_TRY(c, qk::launch_measure_decide(c->d_partials, c->meas_blocks, uniform, c->d_slots, c->d_cbits, dest,
-                                              c->stream));
     }
     {
         LaunchScope ls(c, 4, 4 * half);
@@ -891,13 +891,9 @@ qk_status qk_measure(qk_ctx *c, const int *qubits, int nq, const double *uniform
         ma.n_units = 1ull << (c->n - k);
         {
             LaunchScope ls(c, 5, (double)c->amp * (double)ma.n_units);
+            const qk::Decide d{c->d_counter, uniforms[k], c->d_slots + k, c->d_cbits, dest ? dest[k] : -1};
             CUDA_TRY(c, qk::launch_measure_reduce((int)c->prec, c->d_state, c->n, ma, c->d_slots, c->d_partials,
-                                                  c->meas_blocks, c->stream));
-        }
-        {
-            LaunchScope ls(c, 6, 0);
-            CUDA_TRY(c, qk::launch_measure_decide(c->d_partials, c->meas_blocks, uniforms[k], c->d_slots + k, c->d_cbits,
-                                                  dest ? dest[k] : -1, c->stream));
+                                                  c->meas_blocks, d, c->stream));
         }
     }
     ma.k = nq;

@@ -110,6 +110,63 @@ struct MeasSlot {
     int pad;
 };
 
+// Where a reduction's decision goes.  Every block of the reduction stores its
+// (S0, S1) partials; the last block to finish (an atomic ticket, no waiting) adds
+// all partials in a fixed order, so the result does not depend on timing, and
+// records P0 = S0 / (S0 + S1), the outcome m = (u >= P0), 1/sqrt(S_m) and the cbit.
+struct Decide {
+    unsigned *counter;    // zero between launches; the deciding block resets it
+    double u;
+    MeasSlot *slot;
+    uint8_t *cbits;
+    int dest;             // destination cbit, -1: none
+};
+#ifdef __CUDACC__
+// Called by every thread of every block after thread 0 stored the block's
+// partials[2 * blockIdx.x + {0, 1}].
+__device__ __forceinline__ void last_block_decides(double *partials, const Decide &d) {
+    __shared__ unsigned s_last;
+    __shared__ double s_sum[2][32];
+    if (threadIdx.x == 0) {
+        __threadfence();                     // the partials before the ticket
+        s_last = atomicAdd(d.counter, 1u) == gridDim.x - 1 ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double a0 = 0.0, a1 = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        a0 += __ldcg(&partials[2 * b]);
+        a1 += __ldcg(&partials[2 * b + 1]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_sum[0][threadIdx.x >> 5] = a0;
+        s_sum[1][threadIdx.x >> 5] = a1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            s0 += s_sum[0][w];
+            s1 += s_sum[1][w];
+        }
+        const double tot = s0 + s1;
+        const double p0 = tot > 0.0 ? s0 / tot : 1.0;
+        const int m = (d.u >= p0) ? 1 : 0;
+        const double pm = m ? s1 : s0;
+        d.slot->p0 = p0;
+        d.slot->m = m;
+        d.slot->scale = pm > 0.0 ? 1.0 / sqrt(pm) : 0.0;
+        if (d.dest >= 0) d.cbits[d.dest] = (uint8_t)m;
+        *d.counter = 0;
+    }
+}
+#endif
+
 // Measurement of a list of qubits, one decision at a time.  Decision k sums
 // |a_i|^2 over the indices whose earlier measured bits equal the outcomes
 // already decided (read from the slots on the device), split by bit pos[k].
@@ -254,13 +311,11 @@ cudaError_t launch_matk(int prec, void *psi, const MatKArgs &a, const uint8_t *c
 cudaError_t launch_perm(int prec, const void *in, void *out, const PermArgs &a, const uint8_t *cbits,
                         int sms, cudaStream_t s);
 cudaError_t launch_measure_reduce(int prec, const void *psi, int n, const MeasArgs &a, const MeasSlot *slots,
-                                  double *partials, int nblocks, cudaStream_t s);
-cudaError_t launch_measure_decide(const double *partials, int nblocks, double u, MeasSlot *slot,
-                                  uint8_t *cbits, int dest, cudaStream_t s);
+                                  double *partials, int nblocks, const Decide &d, cudaStream_t s);
 cudaError_t launch_measure_collapse(int prec, void *psi, int n, const MeasArgs &a, const MeasSlot *slots, int sms,
                                     cudaStream_t s);
 cudaError_t launch_kitaev_reduce(int prec, const void *psi, const KitaevArgs &a, const uint8_t *cbits,
-                                 double *partials, int nblocks, cudaStream_t s);
+                                 double *partials, int nblocks, const Decide &d, cudaStream_t s);
 cudaError_t launch_kitaev_update(int prec, const void *psi, void *out, const KitaevArgs &a, const uint8_t *cbits,
                                  const MeasSlot *slot, int sms, cudaStream_t s);
 // K4 on tensor cores (kernels_block_tc.cu): dense 5-qubit complex64 unitary on

@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-pass-per-gate comparison")
     ap.add_argument("--no-kitaev", action="store_true", help="skip the Kitaev order-finding measurement")
     ap.add_argument("--no-block", action="store_true", help="skip the dense 5-qubit block measurement")
+    ap.add_argument("--no-precision", action="store_true", help="skip the complex64-vs-complex128 precision check")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement (0: skip)")
     return ap.parse_args()
 
@@ -362,6 +363,41 @@ def kitaev_measurement(qk, torch, stream, b: int = 20, reps: int = 5):
 
 
 # ---------------------------------------------------------------------------
+# precision of the measured path (the metric's TV bound)
+# ---------------------------------------------------------------------------
+def precision_measurement(qk, torch, stream, n: int, gops):
+    """Total-variation distance and max |a - b| between the complex64 fused state
+    and the complex128 one-pass-per-gate state after the step's gates (before the
+    measurement), both on the GPU at the full size.  The complex128 path is itself
+    checked element by element against the CPU oracle in the parity tests."""
+    a = qk.Context("c64", "fused", stream=stream.cuda_stream)
+    a.add_qubits(n)
+    qk.run_ops(a, gops)
+    va = a.torch_view()
+    a.sync()
+    b = qk.Context("c128", "plain", stream=stream.cuda_stream)
+    b.add_qubits(n)
+    qk.run_ops(b, gops)
+    vb = b.torch_view()
+    b.sync()
+    torch.cuda.synchronize()
+    tv, mx, norm = 0.0, 0.0, 0.0
+    chunk = 1 << 25
+    for s0 in range(0, 1 << n, chunk):
+        x = va[s0:s0 + chunk].to(torch.complex128)
+        y = vb[s0:s0 + chunk]
+        px = x.real * x.real + x.imag * x.imag
+        py = y.real * y.real + y.imag * y.imag
+        tv += float((px - py).abs().sum())
+        norm += float(px.sum())
+        mx = max(mx, float((x - y).abs().max()))
+    a.close()
+    b.close()
+    return {"n": n, "tv": 0.5 * tv, "max_abs": mx, "norm2_c64": norm, "tv_bound": 1e-5, "max_abs_bound": 1e-4,
+            "reference": "complex128 one-pass-per-gate path on the GPU, same gates"}
+
+
+# ---------------------------------------------------------------------------
 # serving (secondary measurement)
 # ---------------------------------------------------------------------------
 def serving_measurement(torch, count: int, rate: float = 200.0):
@@ -532,6 +568,9 @@ def main():
     block = None
     if not args.no_block:
         block = block_measurement(qk, torch, stream, n)
+    precision = None
+    if not args.no_precision and args.mode == "fused":
+        precision = precision_measurement(qk, torch, stream, n, gops)
     serving = None
     if args.serve_requests > 0 and world == 1:
         serving = serving_measurement(torch, args.serve_requests)
@@ -555,6 +594,7 @@ def main():
             "roofline_hbm": roofline_hbm,
             "cpu_baseline": cpu,
             "plain_path": plain,
+            "precision": precision,
             "kitaev": kitaev,
             "block5": block,
             "serving": serving,

@@ -246,25 +246,12 @@ __global__ void __launch_bounds__(kThreads) k_perm(const typename Amp<R>::T *__r
 }
 
 // ---------------------------------------------------------------------------
-// K6: measurement.  reduce -> per-block (S0, S1) in FP64; decide (one block,
-// fixed summation order, so results do not depend on timing); collapse.
-// Per-thread partials of 8 amplitudes are summed in FP32 before entering the
-// FP64 accumulators (GB300's FP64 rate is low; 8-term FP32 sums keep the
-// relative error near 8 ulp of float).
+// K6: measurement.  reduce -> per-block (S0, S1); the last block to finish adds
+// the block partials in a fixed order (so results do not depend on timing) and
+// decides; collapse.  complex64 sums run in compensated FP32 (a float pair that
+// carries each addition's rounding error, about twice float's precision) and
+// reach FP64 once per thread: GB300 has 2 FP64 lanes per SM per clock.
 // ---------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ double block_sum(double v, double *sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
-    return t;  // valid in thread 0
-}
-
 // prefix value of the decided outcomes: sum_j m_j << pos[j], j < k
 __device__ __forceinline__ uint64_t prefix_value(const MeasArgs &a, const MeasSlot *slots, int k) {
     uint64_t v = 0;
@@ -283,38 +270,43 @@ __device__ __forceinline__ uint64_t insert_bits(uint64_t j, const MeasArgs &a) {
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_meas_reduce(const typename Amp<R>::T *__restrict__ psi, MeasArgs a,
                                                           const MeasSlot *slots, double *partials, Decide dec) {
-    __shared__ double sh[kThreads / 32];
+    __shared__ double sh[kThreads];
     const uint64_t pv = prefix_value(a, slots, a.k);
     const int q = a.pos[a.k];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool bit0_free = a.nins == 0 || a.ins[0] != 0;
     double d0 = 0.0, d1 = 0.0;
-    if (sizeof(R) == 4 && bit0_free && a.n_units >= 2) {
-        // two adjacent amplitudes (one 16-byte vector) per unit
-        const uint64_t n_units = a.n_units >> 1;
-        for (uint64_t base = tid; base < n_units; base += 4 * stride) {
-            float f0 = 0.f, f1 = 0.f;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint64_t u = base + (uint64_t)k * stride;
-                if (u < n_units) {
-                    const uint64_t i = insert_bits(u << 1, a) | pv;
-                    const float4 v = *reinterpret_cast<const float4 *>(psi + i);
-                    const float pa = v.x * v.x + v.y * v.y, pb = v.z * v.z + v.w * v.w;
-                    if (q == 0) {
-                        f0 += pa;
-                        f1 += pb;
-                    } else if ((i >> q) & 1u) {
-                        f1 += pa + pb;
-                    } else {
-                        f0 += pa + pb;
-                    }
+    if constexpr (sizeof(R) == 4) {
+        // complex64: |a|^2 in FP32, compensated FP32 running sums (FP64 only per thread)
+        FSum g0, g1;
+        if (bit0_free && a.n_units >= 2) {
+            // two adjacent amplitudes (one 16-byte vector) per unit
+            const uint64_t n_units = a.n_units >> 1;
+#pragma unroll 4
+            for (uint64_t u = tid; u < n_units; u += stride) {
+                const uint64_t i = insert_bits(u << 1, a) | pv;
+                const float4 v = *reinterpret_cast<const float4 *>(psi + i);
+                const float pa = v.x * v.x + v.y * v.y, pb = v.z * v.z + v.w * v.w;
+                if (q == 0) {
+                    g0.add(pa);
+                    g1.add(pb);
+                } else if ((i >> q) & 1u) {
+                    g1.add(pa + pb);
+                } else {
+                    g0.add(pa + pb);
                 }
             }
-            d0 += (double)f0;
-            d1 += (double)f1;
+        } else {
+            for (uint64_t u = tid; u < a.n_units; u += stride) {
+                const uint64_t i = insert_bits(u, a) | pv;
+                const typename Amp<R>::T v = psi[i];
+                const float pa = v.x * v.x + v.y * v.y;
+                if ((i >> q) & 1u) g1.add(pa); else g0.add(pa);
+            }
         }
+        d0 = g0.value();
+        d1 = g1.value();
     } else {
         for (uint64_t u = tid; u < a.n_units; u += stride) {
             const uint64_t i = insert_bits(u, a) | pv;
@@ -323,8 +315,8 @@ __global__ void __launch_bounds__(kThreads) k_meas_reduce(const typename Amp<R>:
             if ((i >> q) & 1u) d1 += pa; else d0 += pa;
         }
     }
-    const double s0 = block_sum<R>(d0, sh);
-    const double s1 = block_sum<R>(d1, sh);
+    const double s0 = block_sum_w0(d0, sh);
+    const double s1 = block_sum_w0(d1, sh);
     if (threadIdx.x == 0) {
         partials[2 * blockIdx.x] = s0;
         partials[2 * blockIdx.x + 1] = s1;

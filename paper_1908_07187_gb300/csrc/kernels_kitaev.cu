@@ -80,45 +80,36 @@ __device__ __forceinline__ double2 block_rphase(const KitaevArgs &a, const uint8
     return s_om;
 }
 
-__device__ __forceinline__ double block_sum(double v, double *sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
-    return t;  // valid in thread 0
-}
-
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_kitaev_reduce(const typename Amp<R>::T *__restrict__ psi, KitaevArgs a,
                                                             const uint8_t *cbits, double *partials, Decide dec) {
-    __shared__ double sh[kThreads / 32];
+    __shared__ double sh[kThreads];
     const double2 om = block_rphase(a, cbits);
     const R wr = (R)om.x, wi = (R)om.y;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // complex64: compensated FP32 sums; complex128: FP64
+    FSum g0, g1;
     double d0 = 0.0, d1 = 0.0;
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; base < a.n_half; base += 4 * stride) {
-        R f0 = 0, f1 = 0;  // short partial sums in the working precision, then FP64
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint64_t j = base + (uint64_t)k * stride;
-            if (j < a.n_half) {
-                const uint64_t i = insert_zero(j, a.cpos);   // control bit 0
-                const typename Amp<R>::T w = psi[i], v = psi[source_index(i, a)];
-                const R tr = wr * v.x - wi * v.y, ti = wr * v.y + wi * v.x;
-                const R pr = w.x + tr, pi = w.y + ti, mr = w.x - tr, mi = w.y - ti;
-                f0 += pr * pr + pi * pi;
-                f1 += mr * mr + mi * mi;
-            }
+#pragma unroll 4
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n_half; j += stride) {
+        const uint64_t i = insert_zero(j, a.cpos);   // control bit 0
+        const typename Amp<R>::T w = psi[i], v = psi[source_index(i, a)];
+        const R tr = wr * v.x - wi * v.y, ti = wr * v.y + wi * v.x;
+        const R pr = w.x + tr, pi = w.y + ti, mr = w.x - tr, mi = w.y - ti;
+        if constexpr (sizeof(R) == 4) {
+            g0.add(pr * pr + pi * pi);
+            g1.add(mr * mr + mi * mi);
+        } else {
+            d0 += pr * pr + pi * pi;
+            d1 += mr * mr + mi * mi;
         }
-        d0 += (double)f0;
-        d1 += (double)f1;
     }
-    const double s0 = block_sum(d0, sh);
-    const double s1 = block_sum(d1, sh);
+    if constexpr (sizeof(R) == 4) {
+        d0 = g0.value();
+        d1 = g1.value();
+    }
+    const double s0 = block_sum_w0(d0, sh);
+    const double s1 = block_sum_w0(d1, sh);
     if (threadIdx.x == 0) {
         partials[2 * blockIdx.x] = s0;
         partials[2 * blockIdx.x + 1] = s1;
@@ -130,11 +121,19 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads) k_kitaev_update(const typename Amp<R>::T *__restrict__ psi,
                                                             typename Amp<R>::T *__restrict__ out, KitaevArgs a,
                                                             const uint8_t *cbits, const MeasSlot *slot) {
-    const double2 om = block_rphase(a, cbits);
-    const int m = slot->m;
-    const R sc = (R)slot->scale;
-    const R sg = m ? (R)-1 : (R)1;
-    const R wr = sg * (R)om.x, wi = sg * (R)om.y;
+    // the decision and the phase, converted to the working precision once per block
+    __shared__ R s_f[3];
+    {
+        const double2 om = block_rphase(a, cbits);
+        if (threadIdx.x == 0) {
+            const double sg = slot->m ? -1.0 : 1.0;
+            s_f[0] = (R)slot->scale;
+            s_f[1] = (R)(sg * om.x);
+            s_f[2] = (R)(sg * om.y);
+        }
+        __syncthreads();
+    }
+    const R sc = s_f[0], wr = s_f[1], wi = s_f[2];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.n_half; j += stride) {
         const uint64_t i = insert_zero(j, a.cpos);

@@ -122,6 +122,36 @@ struct Decide {
     int dest;             // destination cbit, -1: none
 };
 #ifdef __CUDACC__
+// Running sum of FP32 terms kept as an unevaluated pair hi + lo (Knuth's TwoSum:
+// the rounding error of each addition is carried in lo): about twice float's
+// precision at the FP32 rate.  GB300's FP64 rate is too low for an FP64 add per
+// term (2 FP64 lanes per SM per clock).
+struct FSum {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = hi + x;
+        const float bp = s - hi;
+        const float e = (hi - (s - bp)) + (x - bp);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Sum over the block of one double per thread, the FP64 additions done by warp 0
+// alone; sh holds blockDim.x doubles.  The result is valid in thread 0.
+__device__ __forceinline__ double block_sum_w0(double v, double *sh) {
+    __syncthreads();
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        for (int k = threadIdx.x; k < (int)blockDim.x; k += 32) t += sh[k];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;
+}
+
 // Called by every thread of every block after thread 0 stored the block's
 // partials[2 * blockIdx.x + {0, 1}].
 __device__ __forceinline__ void last_block_decides(double *partials, const Decide &d) {

@@ -419,6 +419,11 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     uint32_t *spat = sph + P.nphops * kTileThreads;                              // pattern sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tbits = (warp << 5) | lane;
+    // lanes run over local qubits 0..4 in the load and store arrangements
+    uint64_t lane_off = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+        if ((lane >> j) & 1) lane_off += 1ull << P.S[j];
 
     unsigned condok = 0;
     for (int c = 0; c < P.n_conds; ++c) {
@@ -435,7 +440,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         // load in ARR_IO: lanes = local 0..4, registers = local 5..9, warps = local 10..12
         Regs v;
         {
-            uint64_t tb = (uint64_t)base + (uint64_t)lane;
+            uint64_t tb = (uint64_t)base + lane_off;
 #pragma unroll
             for (int j = 0; j < 3; ++j)
                 if ((warp >> j) & 1) tb += 1ull << P.S[10 + j];
@@ -585,7 +590,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
 
         // store in ARR_IO or ARR_HI (lanes = local 0..4 in both)
         {
-            uint64_t tb = (uint64_t)base + (uint64_t)lane;
+            uint64_t tb = (uint64_t)base + lane_off;
             Offsets<Off> o;
             if (cur == ARR_IO) {
 #pragma unroll

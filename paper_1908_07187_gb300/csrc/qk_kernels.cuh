@@ -245,6 +245,12 @@ struct RelabelArgs {
 // shared memory.  Loads use ARR_IO, stores use ARR_IO or ARR_HI.
 // ---------------------------------------------------------------------------
 constexpr int kTileQubits = 13;
+// Physical qubits 0 .. kTileContig-1 belong to every tile pass, so a warp's loads
+// and stores touch runs of 2^kTileContig contiguous amplitudes; the other tile
+// qubits are chosen freely by the planner.  With 3 the layered 30-qubit circuit
+// needs 10 passes instead of 15 but takes as long: the pass is bound by
+// instruction issue, and its HBM traffic already overlaps the gate arithmetic.
+constexpr int kTileContig = 5;
 constexpr int kTileThreads = 256;
 constexpr int kTileMaxOps = 192;
 constexpr int kTileMaxEntries = 512;

@@ -3,7 +3,8 @@
 // Two gates commute when neither one's non-diagonal qubit (the target of a 2x2
 // gate) is touched by the other; diagonal gates and the control qubits of a
 // controlled gate act diagonally.  A pass picks a set S of 13 physical qubits
-// (always 0..4, for coalesced access) and takes, in order, every queued gate that
+// (always 0 .. kTileContig-1, for coalesced access) and takes, in order, every
+// queued gate that
 //   - is diagonal, or is a 2x2 gate whose target is in S (controls may be
 //     anywhere: a control outside S is constant over a tile), and
 //   - commutes with every earlier gate the pass leaves behind.
@@ -174,8 +175,8 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
     std::vector<POp> left, taken;
     while (!rem.empty()) {
         // ---- choose S and the gates this pass takes
-        uint64_t S = (1ull << 5) - 1;
-        int cnt = 5;
+        uint64_t S = (1ull << kTileContig) - 1;
+        int cnt = kTileContig;
         uint64_t ndb = 0, allb = 0;
         std::vector<Cond> conds;
         left.clear();
@@ -213,7 +214,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             }
         }
         // fill S up to 13 qubits with the lowest unused ones
-        for (int b = 5; b < n && cnt < kTileQubits; ++b)
+        for (int b = kTileContig; b < n && cnt < kTileQubits; ++b)
             if (!((S >> b) & 1)) {
                 S |= 1ull << b;
                 ++cnt;

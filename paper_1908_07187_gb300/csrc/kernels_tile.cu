@@ -36,12 +36,28 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 splat(float x) { return make_float2(x, x); }
 
-// exp(2 pi i t / 2^32)
+// exp(2 pi i j / 256) for j < 256, filled once per CTA
+__shared__ float2 s_turn_tab[256];
+
+__device__ __forceinline__ void fill_turn_table() {
+    for (int j = threadIdx.x; j < 256; j += blockDim.x) {
+        float s, c;
+        sincospif((float)j * (1.f / 128.f), &s, &c);
+        s_turn_tab[j] = make_float2(c, s);
+    }
+}
+
+// exp(2 pi i t / 2^32): the table entry of the top 8 bits times the short
+// Taylor series of the remaining angle x = 2 pi (t mod 2^24) / 2^32 < 2 pi / 256
+// (cos x = 1 - x^2/2 + x^4/24, sin x = x - x^3/6; the next terms are below
+// 2^-30), about a dozen FP32 operations instead of a full sincos.
 __device__ __forceinline__ float2 turns_to_phase(uint32_t t) {
-    const float x = (float)(int32_t)t * 0x1p-31f;  // in [-1, 1): angle = pi * x
-    float s, c;
-    sincospif(x, &s, &c);
-    return make_float2(c, s);
+    const float2 a = s_turn_tab[t >> 24];
+    const float x = (float)(t & 0xFFFFFFu) * 1.46291807926715968e-9f;  // 2 pi / 2^32
+    const float x2 = x * x;
+    const float c = fmaf(x2, fmaf(x2, 1.f / 24.f, -0.5f), 1.f);
+    const float s = x * fmaf(x2, -1.f / 6.f, 1.f);
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
 }
 
 // Amplitudes of one thread: R[j] = (re[2j], re[2j+1]), I[j] = (im[2j], im[2j+1]).
@@ -424,6 +440,9 @@ __global__ void __launch_bounds__(kTileThreads, 2)
 #pragma unroll
     for (int j = 0; j < 5; ++j)
         if ((lane >> j) & 1) lane_off += 1ull << P.S[j];
+
+    fill_turn_table();
+    __syncthreads();
 
     unsigned condok = 0;
     for (int c = 0; c < P.n_conds; ++c) {

@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
+from paper_1908_07187_gb300 import shor  # noqa: E402
 
 METRIC = "30-qubit gates/s & % HBM peak; served circuits/s + p99 vs plain, TV err<=1e-5"
 UNIT = "gates/s"
@@ -357,7 +358,11 @@ def kitaev_measurement(qk, torch, stream, b: int = 20, reps: int = 5):
     graph.close()
     ctx.close()
     res["bits_match"] = bits["generic"] == bits["fused_stage"] == bits["graph"]
-    res["y"] = sum(m << e for e, m in enumerate(bits["fused_stage"]))
+    res["y"] = shor.outcome_from_bits(bits["fused_stage"])
+    # the paper's classical step: continued fractions of y / 2^t, then gcds
+    r = shor.order_from_outcome(res["y"], circ.n_cbits, a, N)
+    res["order"] = r
+    res["factors"] = shor.factors_from_order(a, r, N) if r else None
     res["paper_context"] = "21-qubit Kitaev run of the 20-bit N = 961307 took 139 s on one i5-7400T core (Abstract)"
     return res
 

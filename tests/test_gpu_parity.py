@@ -288,6 +288,31 @@ def test_kitaev_order_finding_bits_exact(qk, b):
         ctx.close()
 
 
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5, 6])
+def test_order_finding_to_factors_n15(qk, seed):
+    # the whole pipeline: fused Kitaev stages on the GPU, then continued fractions
+    # and gcds on the host; for a = 7 the phases are s/4 exactly (r = 4 divides 2^8)
+    from paper_1908_07187_gb300 import shor
+
+    circ = workloads.kitaev_circuit(15, 7, seed=seed)
+    ref = oracle.run_circuit(circ)
+    ctx = qk.Context("c64", "fused")
+    ctx.add_qubits(circ.n_qubits)
+    ctx.add_cbits(circ.n_cbits)
+    qk.run_kitaev_fused(ctx, circ)
+    bits = [int(x) for x in ctx.read_cbits()]
+    ctx.close()
+    assert bits == [int(x) for x in ref.cbits]
+    y = shor.outcome_from_bits(bits)
+    assert y % 64 == 0
+    r = shor.order_from_outcome(y, circ.n_cbits, 7, 15)
+    if y:
+        assert r == 4
+        assert shor.factors_from_order(7, r, 15) == (3, 5)
+    else:
+        assert r is None
+
+
 def test_add_qubits_keeps_state_and_counters(qk):
     psi = workloads.random_state(5, 19)
     ctx = new_ctx(qk, 5, "c64", "plain", psi)

@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-kitaev", action="store_true", help="skip the Kitaev order-finding measurement")
     ap.add_argument("--no-block", action="store_true", help="skip the dense 5-qubit block measurement")
     ap.add_argument("--no-precision", action="store_true", help="skip the complex64-vs-complex128 precision check")
+    ap.add_argument("--batch-circuits", type=int, default=4096, help="circuits in the batched measurement (0: skip)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement (0: skip)")
     return ap.parse_args()
 
@@ -368,6 +369,80 @@ def kitaev_measurement(qk, torch, stream, b: int = 20, reps: int = 5):
 
 
 # ---------------------------------------------------------------------------
+# batched uneven small circuits (secondary measurement)
+# ---------------------------------------------------------------------------
+def batch_measurement(qk, torch, stream, count: int = 4096, seq_sample: int = 24, check_sample: int = 8):
+    """`count` independent U3 + CZ layer circuits of 10..13 qubits (the batch
+    executor's shared-memory limit) and 50..300 layers, all in one batched launch,
+    against running them one after another (one context per circuit, the engine's
+    default mode) on the first `seq_sample` circuits; the batched states of
+    `check_sample` circuits against the complex128 per-gate path (TV distance,
+    max |a - b|)."""
+    import numpy as np
+
+    t0 = time.perf_counter()
+    specs = [workloads.batch_layer_spec(i, n_max=qk.Batch.MAX_QUBITS) for i in range(count)]
+    lists = [qk.layer_gate_ops(*sp) for sp in specs]
+    b = qk.Batch(stream=stream.cuda_stream)
+    for sp, ops in zip(specs, lists):
+        b.add_circuit(sp[0], 0)
+        b.apply_gates(ops)
+    t_build = time.perf_counter() - t0
+    gates = int(sum(len(x) for x in lists))
+    b.run(store_states=True)                      # warm-up (uploads, first launch)
+    while not b.done():
+        time.sleep(0.0005)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.run(store_states=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    tv, mx = 0.0, 0.0
+    for i in range(check_sample):
+        n, depth, ang = specs[i]
+        ref = qk.Context("c128", "plain", stream=stream.cuda_stream)
+        ref.add_qubits(n)
+        qk.run_ops(ref, workloads.layer_spec_circuit(n, depth, ang).ops)
+        want = ref.get_state()
+        ref.close()
+        got = b.read(i)[1].astype(np.complex128)
+        tv = max(tv, 0.5 * float(np.abs(np.abs(got) ** 2 - np.abs(want) ** 2).sum()))
+        mx = max(mx, float(np.abs(got - want).max()))
+    b.close()
+    # one circuit after another, one context each
+    circs = [workloads.layer_spec_circuit(*specs[i]) for i in range(seq_sample)]
+    ctxs = []
+    for c in circs:
+        ctx = qk.Context("c64", "fused", stream=stream.cuda_stream)
+        ctx.add_qubits(c.n_qubits)
+        ctxs.append(ctx)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_p = time.perf_counter()
+    p0.record(stream)
+    for ctx, c in zip(ctxs, circs):
+        qk.run_ops(ctx, c.ops)
+        ctx.flush()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    t_seq_host = time.perf_counter() - t_p
+    seq_ms = p0.elapsed_time(p1)
+    for ctx in ctxs:
+        ctx.close()
+    batched_cps = count / (ms / 1000.0)
+    seq_cps = seq_sample / max(seq_ms / 1000.0, t_seq_host)
+    return {"circuits": count, "qubits": f"10..{qk.Batch.MAX_QUBITS}", "layers": "50..300", "gates": gates,
+            "batched": {"ms": round(ms, 3), "circuits_per_s": round(batched_cps, 1),
+                        "gates_per_s": round(gates / (ms / 1000.0), 1), "host_build_s": round(t_build, 2)},
+            "one_by_one": {"circuits": seq_sample, "circuits_per_s": round(seq_cps, 2),
+                           "note": "wall time (host marshalling included) of the first circuits run one after another"},
+            "speedup_circuits_per_s": round(batched_cps / seq_cps, 1),
+            "precision": {"circuits_checked": check_sample, "tv_max": tv, "max_abs": mx,
+                          "reference": "complex128 one-pass-per-gate path on the GPU"}}
+
+
+# ---------------------------------------------------------------------------
 # precision of the measured path (the metric's TV bound)
 # ---------------------------------------------------------------------------
 def precision_measurement(qk, torch, stream, n: int, gops):
@@ -573,6 +648,9 @@ def main():
     block = None
     if not args.no_block:
         block = block_measurement(qk, torch, stream, n)
+    batch = None
+    if args.batch_circuits > 0 and world == 1:
+        batch = batch_measurement(qk, torch, stream, args.batch_circuits)
     precision = None
     if not args.no_precision and args.mode == "fused":
         precision = precision_measurement(qk, torch, stream, n, gops)
@@ -597,11 +675,17 @@ def main():
             "state_passes_per_step": counters["state_passes"] / args.steps,
             "roofline": roofline,
             "roofline_hbm": roofline_hbm,
+            # what one-pass-per-gate execution would have to stream for the same gates/s
+            "gate_equivalent_bandwidth": {
+                "GBps": round(value * 2 * 8 * (1 << n) / 1e9, 1),
+                "x_measured_hbm_peak": round(value * 2 * 8 * (1 << n) / 1e9 / peak, 2),
+                "unfused_plain_path_GBps": round(plain["value"] * 2 * 8 * (1 << n) / 1e9, 1) if plain else None},
             "cpu_baseline": cpu,
             "plain_path": plain,
             "precision": precision,
             "kitaev": kitaev,
             "block5": block,
+            "batched": batch,
             "serving": serving,
             "launch_profile": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items() if v["launches"]},
             "clocks": clk,

@@ -280,6 +280,23 @@ qk_status qk_batch_apply_gate(qk_batch *b, int gate_id, const int *targets, int 
                               const int *cond_cbits, int ncc, const double *params, int np);
 qk_status qk_batch_apply_mulmod(qk_batch *b, const int *targets, int w, const int *controls, int nc, uint64_t c,
                                 uint64_t N);
+/* One entry of a gate list for qk_batch_apply_gates: a built-in 1-target gate
+ * with up to 4 quantum controls, up to 4 condition cbits and up to 3 parameters
+ * (the meaning of each field as in qk_batch_apply_gate).  Plain C layout,
+ * 80 bytes. */
+typedef struct qk_gate_op {
+    int gate_id;
+    int target;
+    int nc, ncc, np;
+    int controls[4];
+    int cond[4];
+    double params[3];
+} qk_gate_op;
+/* Append `count` gates to the most recently added circuit, in order; the same
+ * checks and errors as one qk_batch_apply_gate call per entry (on an error the
+ * entries before the bad one stay appended and the message names its index).
+ * The list is copied before the call returns. */
+qk_status qk_batch_apply_gates(qk_batch *b, const qk_gate_op *ops, int count);
 qk_status qk_batch_measure(qk_batch *b, const int *qubits, int nq, const double *uniforms, const int *dest_cbits);
 qk_status qk_batch_run(qk_batch *b, int store_states);
 /* 1 when the last run has finished, 0 while it runs, -1 on error. */

@@ -389,6 +389,23 @@ qk_status qk_batch_apply_gate(qk_batch *b, int gate_id, const int *targets, int 
     return QK_OK;
 }
 
+qk_status qk_batch_apply_gates(qk_batch *b, const qk_gate_op *ops, int count) {
+    if (!b) return QK_EINVAL;
+    if (count < 0 || (count > 0 && !ops)) return bfail(b, QK_EINVAL, "batch: bad gate list");
+    for (int i = 0; i < count; ++i) {
+        const qk_gate_op &g = ops[i];
+        if (g.nc < 0 || g.nc > 4 || g.ncc < 0 || g.ncc > 4 || g.np < 0 || g.np > 3)
+            return bfail(b, QK_EINVAL, "batch: gate list entry %d has bad counts", i);
+        const qk_status st =
+            qk_batch_apply_gate(b, g.gate_id, &g.target, 1, g.controls, g.nc, g.cond, g.ncc, g.params, g.np);
+        if (st != QK_OK) {
+            const std::string msg = b->err;
+            return bfail(b, st, "batch: gate list entry %d: %s", i, msg.c_str());
+        }
+    }
+    return QK_OK;
+}
+
 qk_status qk_batch_apply_mulmod(qk_batch *b, const int *targets, int w, const int *controls, int nc, uint64_t cc,
                                 uint64_t N) {
     if (!b) return QK_EINVAL;

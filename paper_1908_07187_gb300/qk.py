@@ -33,6 +33,38 @@ GATE = {
 }
 
 
+# qk_gate_op (include/qk.h): one entry of a batch gate list, C layout
+GATE_OP_DTYPE = np.dtype([("gate_id", np.int32), ("target", np.int32), ("nc", np.int32), ("ncc", np.int32),
+                          ("np", np.int32), ("controls", np.int32, 4), ("cond", np.int32, 4),
+                          ("params", np.float64, 3)], align=True)
+assert GATE_OP_DTYPE.itemsize == 80
+
+
+def layer_gate_ops(n: int, depth: int, angles) -> np.ndarray:
+    """The gate list of a U3 + CZ layer circuit as qk_gate_op entries (marshalling
+    only): layer L is U3(angles[L, q]) on every qubit q, then CZ on the pairs
+    (q, q+1) with q = L mod 2, L mod 2 + 2, ..."""
+    angles = np.asarray(angles, dtype=np.float64).reshape(depth, n, 3)
+    per = [n + len(range(L % 2, n - 1, 2)) for L in range(depth)]
+    out = np.zeros(sum(per), dtype=GATE_OP_DTYPE)
+    pos = 0
+    for L in range(depth):
+        u = out[pos:pos + n]
+        u["gate_id"] = GATE["u3"]
+        u["target"] = np.arange(n)
+        u["np"] = 3
+        u["params"] = angles[L]
+        pos += n
+        qs = np.arange(L % 2, n - 1, 2)
+        z = out[pos:pos + len(qs)]
+        z["gate_id"] = GATE["z"]
+        z["target"] = qs + 1
+        z["nc"] = 1
+        z["controls"][:, 0] = qs
+        pos += len(qs)
+    return out
+
+
 class Options(ctypes.Structure):
     _fields_ = [("exec_mode", ctypes.c_int), ("tile_qubits", ctypes.c_int), ("max_pending", ctypes.c_int),
                 ("profile", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t),
@@ -86,6 +118,7 @@ _SIGS = {
                              ctypes.c_int], ctypes.c_int),
     "qk_batch_apply_mulmod": ([_P, _IP, ctypes.c_int, _IP, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64],
                               ctypes.c_int),
+    "qk_batch_apply_gates": ([_P, _P, ctypes.c_int], ctypes.c_int),
     "qk_batch_measure": ([_P, _IP, ctypes.c_int, _DP, _IP], ctypes.c_int),
     "qk_batch_run": ([_P, ctypes.c_int], ctypes.c_int),
     "qk_batch_done": ([_P], ctypes.c_int),
@@ -389,6 +422,11 @@ class Batch:
         t, nt = _ints(targets)
         cl, nc = _ints(controls)
         self._check(_lib.qk_batch_apply_mulmod(self._h, t, nt, cl, nc, c, N))
+
+    def apply_gates(self, ops: np.ndarray):
+        """A whole gate list (GATE_OP_DTYPE entries) in one call."""
+        arr = np.ascontiguousarray(ops, dtype=GATE_OP_DTYPE)
+        self._check(_lib.qk_batch_apply_gates(self._h, arr.ctypes.data, len(arr)))
 
     def measure(self, qubits, uniforms, dest=None):
         q, nq = _ints(qubits)

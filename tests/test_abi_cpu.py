@@ -70,3 +70,28 @@ def test_product_package_does_not_import_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
                 assert "qk_oracle" not in src and "liboracle" not in src, f
+
+
+def test_gate_op_layout_matches_the_header(tmp_path):
+    # compile a probe against include/qk.h and compare the C layout of
+    # qk_gate_op with the binding's numpy dtype
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "probe.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "qk.h"\n'
+        "int main(void) { printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(qk_gate_op),"
+        " offsetof(qk_gate_op, target), offsetof(qk_gate_op, np), offsetof(qk_gate_op, controls),"
+        " offsetof(qk_gate_op, cond), offsetof(qk_gate_op, params)); return 0; }\n")
+    exe = tmp_path / "probe"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    from paper_1908_07187_gb300 import qk
+
+    dt = qk.GATE_OP_DTYPE
+    assert got == [dt.itemsize, dt.fields["target"][1], dt.fields["np"][1], dt.fields["controls"][1],
+                   dt.fields["cond"][1], dt.fields["params"][1]]

@@ -103,3 +103,39 @@ def test_batch_mulmod_and_conditions(qk):
     with pytest.raises(qk.QKError):
         b.apply_mulmod([1, 2, 3], [0], 5, 15)   # N > 2^w
     b.close()
+
+
+def test_gate_list_call_matches_per_gate_calls_and_oracle(qk):
+    # the bulk qk_batch_apply_gates path for U3 + CZ layer circuits of uneven size
+    specs = [workloads.batch_layer_spec(i, seed=11, n_max=13, d_min=3, d_max=12) for i in range(6)]
+    bulk, single = qk.Batch(), qk.Batch()
+    for n, depth, ang in specs:
+        bulk.add_circuit(n, 0)
+        bulk.apply_gates(qk.layer_gate_ops(n, depth, ang))
+        c = workloads.layer_spec_circuit(n, depth, ang)
+        single.add_ops(c.n_qubits, 0, c.ops)
+    bulk.run()
+    single.run()
+    for i, (n, depth, ang) in enumerate(specs):
+        got = bulk.read(i)[1]
+        assert np.array_equal(got, single.read(i)[1])
+        ref = oracle.run_circuit(workloads.layer_spec_circuit(n, depth, ang))
+        np.testing.assert_allclose(got, ref.psi, atol=1e-4)
+        assert 0.5 * np.abs(np.abs(got) ** 2 - np.abs(ref.psi) ** 2).sum() < 1e-5
+    bulk.close()
+    single.close()
+
+
+def test_gate_list_rejects_bad_entries(qk):
+    b = qk.Batch()
+    b.add_circuit(4, 0)
+    ops = qk.layer_gate_ops(4, 1, np.zeros((1, 4, 3)))
+    ops[2]["target"] = 9                       # outside the 4-qubit circuit
+    with pytest.raises(qk.QKError) as e:
+        b.apply_gates(ops)
+    assert e.value.status == qk.QK_EINVAL and "entry 2" in str(e.value)
+    ops = qk.layer_gate_ops(4, 1, np.zeros((1, 4, 3)))
+    ops[0]["nc"] = 7
+    with pytest.raises(qk.QKError):
+        b.apply_gates(ops)
+    b.close()

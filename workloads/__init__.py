@@ -194,6 +194,31 @@ def layered_circuit(n: int, seed: int = 2, n_gates: int = 500, qft: bool = True,
     return Circuit(n, n_cb, ops, name=f"layered{n}q_{n_gates}g_seed{seed}")
 
 
+def batch_layer_spec(index: int, seed: int = 4, n_min: int = 10, n_max: int = 20,
+                     d_min: int = 50, d_max: int = 300):
+    """One circuit of the batched workload: n ~ U{n_min..n_max} qubits, depth ~
+    U{d_min..d_max} layers, each layer U3(theta, phi, lambda ~ U[0, 2 pi)) on every
+    qubit then CZ on the even (even layers) or odd (odd layers) neighbour pairs.
+    Returns (n, depth, angles[depth, n, 3]); numpy's PCG64 keyed by (seed, index)
+    keeps thousands of circuits cheap to draw."""
+    import numpy as np
+
+    rng = np.random.Generator(np.random.PCG64([seed, index]))
+    n = int(rng.integers(n_min, n_max + 1))
+    depth = int(rng.integers(d_min, d_max + 1))
+    angles = rng.uniform(0.0, 2.0 * math.pi, size=(depth, n, 3))
+    return n, depth, angles
+
+
+def layer_spec_circuit(n: int, depth: int, angles) -> Circuit:
+    """The ops of a batch_layer_spec circuit (for the oracle and per-gate paths)."""
+    ops: List[Op] = []
+    for L in range(depth):
+        ops += [Op("u3", (q,), params=tuple(float(a) for a in angles[L][q])) for q in range(n)]
+        ops += [Op("z", (q + 1,), controls=(q,)) for q in range(L % 2, n - 1, 2)]
+    return Circuit(n, 0, ops, name=f"layers{n}q_{depth}d")
+
+
 # ---------------------------------------------------------------------------
 # Kitaev order finding inputs
 # ---------------------------------------------------------------------------

@@ -118,10 +118,14 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_sha():
+# the sources that decide each kernel class's memory traffic
+KERNEL_SOURCES = {"tile": ("kernels_tile.cu", "qk_kernels.cuh", "qk_plan.cu")}
+
+
+def kernel_source_sha(kernel_class: str = "tile"):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1908_07187_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES.get(kernel_class, sorted(os.listdir(csrc))):
         if f.endswith((".cu", ".cuh", ".h")):
             with open(os.path.join(csrc, f), "rb") as fh:
                 h.update(fh.read())
@@ -136,7 +140,7 @@ def recorded_traffic(kernel_class: str, n: int):
         with open(path) as fh:
             d = json.load(fh)
         rec = d.get(f"{kernel_class}_n{n}")
-        if rec and rec.get("src_sha") == kernel_source_sha():
+        if rec and rec.get("src_sha") == kernel_source_sha(kernel_class):
             return float(rec["dram_bytes_per_launch"])
     except Exception:
         pass

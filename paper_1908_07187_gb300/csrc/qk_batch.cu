@@ -24,6 +24,7 @@
 
 #include "qk.h"
 #include "qk_host.h"
+#include "qk_kernels.cuh"
 
 namespace qk {
 namespace {
@@ -31,6 +32,7 @@ namespace {
 constexpr int kBThreads = 256;
 constexpr int kBMaxQubits = 13;
 constexpr int kBMaxCbits = 64;
+constexpr int kOpChunk = kBThreads * 16 / 64;   // ops staged per chunk: one 16-byte word per thread
 
 enum BOpKind : uint8_t { B_U2 = 0, B_PHASE = 1, B_MULMOD = 2, B_MEASURE = 3 };
 
@@ -61,7 +63,7 @@ struct BCirc {
     uint32_t op_begin, op_end;
     uint32_t n, ncb;
     uint32_t cb_off;
-    uint32_t pad;
+    uint32_t flags;            // bit 0: holds a mul-mod (needs the second state buffer)
     uint64_t state_off;        // in amplitudes
 };
 
@@ -81,6 +83,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BCirc *__restrict__ c
     __shared__ uint8_t cb[kBMaxCbits];
     __shared__ int s_m;
     __shared__ float s_scale;
+    __shared__ __align__(16) BOp s_ops[2][kOpChunk];
     float2 *A = reinterpret_cast<float2 *>(sm);
     float2 *B = A + dim;
     const int tid = threadIdx.x;
@@ -88,92 +91,112 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BCirc *__restrict__ c
     for (int k = tid; k < kBMaxCbits; k += kBThreads) cb[k] = 0;
     __syncthreads();
 
-    for (uint32_t oi = c.op_begin; oi < c.op_end; ++oi) {
-        const BOp &op = ops[oi];
-        bool act = true;
-        for (int k = 0; k < op.ncond; ++k) act = act && cb[op.cond[k]] != 0;
-        if (op.kind == B_U2) {
-            if (act) {
-                const float2 m00 = make_float2(op.m[0], op.m[1]), m01 = make_float2(op.m[2], op.m[3]);
-                const float2 m10 = make_float2(op.m[4], op.m[5]), m11 = make_float2(op.m[6], op.m[7]);
-                for (uint32_t p = tid; p < (dim >> 1); p += kBThreads) {
-                    const uint32_t i0 = ins0(p, op.q), i1 = i0 | (1u << op.q);
-                    if ((i0 & op.cmask) != op.cmask) continue;
-                    const float2 a = A[i0], b = A[i1];
-                    A[i0] = make_float2(m00.x * a.x - m00.y * a.y + m01.x * b.x - m01.y * b.y,
-                                        m00.x * a.y + m00.y * a.x + m01.x * b.y + m01.y * b.x);
-                    A[i1] = make_float2(m10.x * a.x - m10.y * a.y + m11.x * b.x - m11.y * b.y,
-                                        m10.x * a.y + m10.y * a.x + m11.x * b.y + m11.y * b.x);
-                }
-            }
-        } else if (op.kind == B_PHASE) {
-            if (act) {
-                const float fr = op.ph.re, fi = op.ph.im;
-                for (uint32_t i = tid; i < dim; i += kBThreads)
-                    if ((i & op.cmask) == op.val) {
-                        const float2 a = A[i];
-                        A[i] = make_float2(a.x * fr - a.y * fi, a.x * fi + a.y * fr);
+    // the program streams through shared memory in chunks of kOpChunk ops (one
+    // 16-byte load per thread per chunk); the next chunk's load is issued before
+    // the current chunk runs, so its latency hides behind the gates
+    const uint32_t nops = c.op_end - c.op_begin;
+    const uint4 *gops = reinterpret_cast<const uint4 *>(ops + c.op_begin);
+    const uint32_t nwords = nops * (uint32_t)(sizeof(BOp) / 16);
+    if ((uint32_t)tid < nwords) reinterpret_cast<uint4 *>(s_ops[0])[tid] = gops[tid];
+    __syncthreads();
+    for (uint32_t chunk = 0; chunk * kOpChunk < nops; ++chunk) {
+        const int buf = (int)(chunk & 1);
+        const uint32_t nw = (chunk + 1) * kOpChunk * (uint32_t)(sizeof(BOp) / 16) + (uint32_t)tid;
+        uint4 next = make_uint4(0, 0, 0, 0);
+        if (nw < nwords) next = gops[nw];
+        const uint32_t cnt = min((uint32_t)kOpChunk, nops - chunk * kOpChunk);
+        for (uint32_t oi = 0; oi < cnt; ++oi) {
+            const BOp &op = s_ops[buf][oi];
+            bool act = true;
+            for (int k = 0; k < op.ncond; ++k) act = act && cb[op.cond[k]] != 0;
+            if (op.kind == B_U2) {
+                if (act) {
+                    const float2 m00 = make_float2(op.m[0], op.m[1]), m01 = make_float2(op.m[2], op.m[3]);
+                    const float2 m10 = make_float2(op.m[4], op.m[5]), m11 = make_float2(op.m[6], op.m[7]);
+                    for (uint32_t p = tid; p < (dim >> 1); p += kBThreads) {
+                        const uint32_t i0 = ins0(p, op.q), i1 = i0 | (1u << op.q);
+                        if ((i0 & op.cmask) != op.cmask) continue;
+                        const float2 a = A[i0], b = A[i1];
+                        A[i0] = make_float2(m00.x * a.x - m00.y * a.y + m01.x * b.x - m01.y * b.y,
+                                            m00.x * a.y + m00.y * a.x + m01.x * b.y + m01.y * b.x);
+                        A[i1] = make_float2(m10.x * a.x - m10.y * a.y + m11.x * b.x - m11.y * b.y,
+                                            m10.x * a.y + m10.y * a.x + m11.x * b.y + m11.y * b.x);
                     }
-            }
-        } else if (op.kind == B_MULMOD) {
-            for (uint32_t i = tid; i < dim; i += kBThreads) {
-                uint32_t src = i;
-                if (act && (i & op.cmask) == op.cmask) {
-                    uint32_t y = 0;
-                    for (int b = 0; b < op.w; ++b) y = (y << 1) | ((i >> op.mm.rpos[b]) & 1u);
-                    if (y < op.mm.N) {
-                        const uint32_t x = (uint32_t)(((uint64_t)op.mm.cinv * y) % op.mm.N);
-                        for (int b = 0; b < op.w; ++b) {
-                            const uint32_t bit = (x >> (op.w - 1 - b)) & 1u;
-                            src = (src & ~(1u << op.mm.rpos[b])) | (bit << op.mm.rpos[b]);
+                }
+            } else if (op.kind == B_PHASE) {
+                if (act) {
+                    const float fr = op.ph.re, fi = op.ph.im;
+                    for (uint32_t i = tid; i < dim; i += kBThreads)
+                        if ((i & op.cmask) == op.val) {
+                            const float2 a = A[i];
+                            A[i] = make_float2(a.x * fr - a.y * fi, a.x * fi + a.y * fr);
+                        }
+                }
+            } else if (op.kind == B_MULMOD) {
+                for (uint32_t i = tid; i < dim; i += kBThreads) {
+                    uint32_t src = i;
+                    if (act && (i & op.cmask) == op.cmask) {
+                        uint32_t y = 0;
+                        for (int b = 0; b < op.w; ++b) y = (y << 1) | ((i >> op.mm.rpos[b]) & 1u);
+                        if (y < op.mm.N) {
+                            const uint32_t x = (uint32_t)(((uint64_t)op.mm.cinv * y) % op.mm.N);
+                            for (int b = 0; b < op.w; ++b) {
+                                const uint32_t bit = (x >> (op.w - 1 - b)) & 1u;
+                                src = (src & ~(1u << op.mm.rpos[b])) | (bit << op.mm.rpos[b]);
+                            }
                         }
                     }
+                    B[i] = A[src];
                 }
-                B[i] = A[src];
-            }
-            __syncthreads();
-            float2 *t = A;
-            A = B;
-            B = t;
-        } else {  // B_MEASURE on qubit q
-            double d0 = 0.0, d1 = 0.0;
-            for (uint32_t i = tid; i < dim; i += kBThreads) {
-                const float2 a = A[i];
-                const double pa = (double)a.x * a.x + (double)a.y * a.y;
-                if ((i >> op.q) & 1u) d1 += pa; else d0 += pa;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-                d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-            }
-            if ((tid & 31) == 0) {
-                red[0][tid >> 5] = d0;
-                red[1][tid >> 5] = d1;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                double s0 = 0.0, s1 = 0.0;
-                for (int w = 0; w < kBThreads / 32; ++w) {
-                    s0 += red[0][w];
-                    s1 += red[1][w];
+                __syncthreads();
+                float2 *t = A;
+                A = B;
+                B = t;
+            } else {  // B_MEASURE on qubit q
+                // |a|^2 in FP32 into compensated float pairs (GB300 has 2 FP64 lanes per
+                // SM per clock), FP64 from the per-thread sums on
+                FSum g0, g1;
+                for (uint32_t i = tid; i < dim; i += kBThreads) {
+                    const float2 a = A[i];
+                    const float pa = a.x * a.x + a.y * a.y;
+                    if ((i >> op.q) & 1u) g1.add(pa); else g0.add(pa);
                 }
-                const double tot = s0 + s1;
-                const double p0 = tot > 0.0 ? s0 / tot : 1.0;
-                const int m = (op.ms.u >= p0) ? 1 : 0;
-                const double pm = m ? s1 : s0;
-                s_m = m;
-                s_scale = (float)(pm > 0.0 ? 1.0 / sqrt(pm) : 0.0);
-                if (op.ms.dest >= 0) cb[op.ms.dest] = (uint8_t)m;
+                double d0 = g0.value(), d1 = g1.value();
+                for (int o = 16; o > 0; o >>= 1) {
+                    d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+                    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+                }
+                if ((tid & 31) == 0) {
+                    red[0][tid >> 5] = d0;
+                    red[1][tid >> 5] = d1;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    double s0 = 0.0, s1 = 0.0;
+                    for (int w = 0; w < kBThreads / 32; ++w) {
+                        s0 += red[0][w];
+                        s1 += red[1][w];
+                    }
+                    const double tot = s0 + s1;
+                    const double p0 = tot > 0.0 ? s0 / tot : 1.0;
+                    const int m = (op.ms.u >= p0) ? 1 : 0;
+                    const double pm = m ? s1 : s0;
+                    s_m = m;
+                    s_scale = (float)(pm > 0.0 ? 1.0 / sqrt(pm) : 0.0);
+                    if (op.ms.dest >= 0) cb[op.ms.dest] = (uint8_t)m;
+                }
+                __syncthreads();
+                const int m = s_m;
+                const float sc = s_scale;
+                for (uint32_t i = tid; i < dim; i += kBThreads) {
+                    const float k = ((int)((i >> op.q) & 1u) == m) ? sc : 0.f;
+                    const float2 a = A[i];
+                    A[i] = make_float2(a.x * k, a.y * k);
+                }
             }
             __syncthreads();
-            const int m = s_m;
-            const float sc = s_scale;
-            for (uint32_t i = tid; i < dim; i += kBThreads) {
-                const float k = ((int)((i >> op.q) & 1u) == m) ? sc : 0.f;
-                const float2 a = A[i];
-                A[i] = make_float2(a.x * k, a.y * k);
-            }
         }
+        if (nw < nwords) reinterpret_cast<uint4 *>(s_ops[buf ^ 1])[tid] = next;
         __syncthreads();
     }
     for (uint32_t k = tid; k < c.ncb; k += kBThreads) cbits_out[c.cb_off + k] = cb[k];
@@ -430,6 +453,7 @@ qk_status qk_batch_apply_mulmod(qk_batch *b, const int *targets, int w, const in
     }
     op.mm.N = (uint32_t)N;
     op.mm.cinv = (uint32_t)inv;
+    c->flags |= 1u;
     b->ops.push_back(op);
     c->op_end = (uint32_t)b->ops.size();
     return QK_OK;
@@ -476,10 +500,13 @@ qk_status qk_batch_run(qk_batch *b, int store_states) {
         }
         b->cap_stage = (ob + cb) * 2;
     }
-    // circuits sorted by size: one launch per qubit count, each sized to its
+    // circuits sorted by size: one launch per qubit count (and per need of the
+    // second state buffer, which only mul-mod gathers use), each sized to its
     // shared memory (small circuits then share an SM)
     std::vector<qk::BCirc> sorted(b->circs);
-    std::stable_sort(sorted.begin(), sorted.end(), [](const qk::BCirc &x, const qk::BCirc &y) { return x.n < y.n; });
+    std::stable_sort(sorted.begin(), sorted.end(), [](const qk::BCirc &x, const qk::BCirc &y) {
+        return x.n != y.n ? x.n < y.n : (x.flags & 1u) < (y.flags & 1u);
+    });
     std::memcpy(b->h_stage, b->ops.data(), ob);
     std::memcpy((char *)b->h_stage + ob, sorted.data(), cb);
     if (cudaMemcpyAsync(b->d_ops, b->h_stage, ob, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
@@ -491,8 +518,9 @@ qk_status qk_batch_run(qk_batch *b, int store_states) {
         return bfail(b, QK_ECUDA, "batch: shared memory attribute failed");
     for (size_t i = 0; i < sorted.size();) {
         size_t j = i;
-        while (j < sorted.size() && sorted[j].n == sorted[i].n) ++j;
-        const size_t smem = sizeof(float2) * 2 * ((size_t)1 << sorted[i].n);
+        while (j < sorted.size() && sorted[j].n == sorted[i].n && (sorted[j].flags & 1u) == (sorted[i].flags & 1u))
+            ++j;
+        const size_t smem = sizeof(float2) * ((sorted[i].flags & 1u) ? 2 : 1) * ((size_t)1 << sorted[i].n);
         qk::k_batch<<<(unsigned)(j - i), qk::kBThreads, smem, b->stream>>>(b->d_circs + i, b->d_ops, b->d_states,
                                                                           b->d_cbits, b->store_state ? 1 : 0);
         if (cudaGetLastError() != cudaSuccess) return bfail(b, QK_ECUDA, "batch: launch failed");

@@ -41,7 +41,7 @@ struct ProfRec {
     double bytes;
 };
 
-constexpr int kMeasBlocksPerSM = 4;
+constexpr int kMeasBlocksPerSM = 8;   // measurement reductions: enough loads in flight for HBM
 
 }  // namespace
 
@@ -852,8 +852,10 @@ qk_status qk_apply_kitaev_stage(qk_ctx *c, int control, int gate_id, const int *
     {
         LaunchScope ls(c, 4, 2 * half);
         const qk::Decide d{c->d_counter, uniform, c->d_slots, c->d_cbits, dest};
-        CUDA_TRY(c, qk::launch_kitaev_reduce((int)c->prec, c->d_state, a, c->d_cbits, c->d_partials, c->meas_blocks, d,
-                                             c->stream));
+        // half the measurement grid: the stage's state sits in L2 and a longer grid
+        // only adds partials for the deciding block to add
+        CUDA_TRY(c, qk::launch_kitaev_reduce((int)c->prec, c->d_state, a, c->d_cbits, c->d_partials,
+                                             c->meas_blocks / 2, d, c->stream));
     }
     {
         LaunchScope ls(c, 4, 4 * half);

@@ -271,21 +271,37 @@ struct Pending {
             for (int k = 0; k < 5; ++k)
                 fa[k * kTileThreads] = (mask & (1 << k)) ? turns_to_phase(t(k)) : make_float2(1.f, 0.f);
             const float2 a0 = fa[0];
-            float2 d = c0;
+            // four independent chains over register bits 1, 2 (j = 4h + l, l < 4),
+            // started at c0 * (a3, a4 products of h): dependency depth 4, not 16
+            float2 d[4];
+            {
+                const float2 a3 = fa[3 * kTileThreads], a4 = fa[4 * kTileThreads];
+                d[0] = c0;
+                d[1] = cmul(c0, a3);
+                d[2] = cmul(c0, a4);
+                d[3] = cmul(d[1], a4);
+            }
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int g = i ^ (i >> 1);
-                if (i > 0) {
-                    const int gp = (i - 1) ^ ((i - 1) >> 1);
-                    const int b = ctz_const(g ^ gp);         // register bit b + 1 toggles
-                    const float2 ab = fa[(b + 1) * kTileThreads];
-                    d = cmul(d, (g >> b) & 1 ? ab : make_float2(ab.x, -ab.y));
+            for (int l = 0; l < 4; ++l) {
+                // l walks 0, 1, 3, 2 (Gray order over bits 1 and 2)
+                const int g = l ^ (l >> 1);
+                if (l > 0) {
+                    const int gp = (l - 1) ^ ((l - 1) >> 1);
+                    const int bb = ctz_const(g ^ gp);      // register bit bb + 1 toggles
+                    const float2 ab = fa[(bb + 1) * kTileThreads];
+                    const float2 f = (g >> bb) & 1 ? ab : make_float2(ab.x, -ab.y);
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) d[h] = cmul(d[h], f);
                 }
-                const float2 d1 = cmul(d, a0);
-                const float2 Dr = make_float2(d.x, d1.x), Di = make_float2(d.y, d1.y);
-                const float2 A = v.R[g], B = v.I[g];
-                v.R[g] = __ffma2_rn(make_float2(-Di.x, -Di.y), B, __fmul2_rn(Dr, A));
-                v.I[g] = __ffma2_rn(Di, A, __fmul2_rn(Dr, B));
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int j = 4 * h + g;
+                    const float2 d1 = cmul(d[h], a0);
+                    const float2 Dr = make_float2(d[h].x, d1.x), Di = make_float2(d[h].y, d1.y);
+                    const float2 A = v.R[j], B = v.I[j];
+                    v.R[j] = __ffma2_rn(make_float2(-Di.x, -Di.y), B, __fmul2_rn(Dr, A));
+                    v.I[j] = __ffma2_rn(Di, A, __fmul2_rn(Dr, B));
+                }
             }
         }
         reset();

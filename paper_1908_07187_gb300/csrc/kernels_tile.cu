@@ -428,13 +428,13 @@ template <typename Off, int... rs>
 __device__ __forceinline__ void load_all(const float2 *src, const Offsets<Off> &o, Regs &v,
                                          std::integer_sequence<int, rs...>) {
     float2 tmp[32];
-    ((tmp[rs] = __ldcs(src + o.template at<rs>())), ...);
+    ((tmp[rs] = __ldcg(src + o.template at<rs>())), ...);
     ((re_of<rs>(v) = tmp[rs].x, im_of<rs>(v) = tmp[rs].y), ...);
 }
 template <typename Off, int... rs>
 __device__ __forceinline__ void store_all(float2 *dst, const Offsets<Off> &o, Regs &v,
                                           std::integer_sequence<int, rs...>) {
-    (__stcs(dst + o.template at<rs>(), make_float2(re_of<rs>(v), im_of<rs>(v))), ...);
+    ((dst[o.template at<rs>()] = make_float2(re_of<rs>(v), im_of<rs>(v))), ...);
 }
 
 template <typename Off>
@@ -657,11 +657,16 @@ cudaError_t launch_tile_t(void *psi, const TileParams &p, const TileEntries *ent
         ((int)(2 * sizeof(float)) << kTileQubits) + (16 + kTileMaxPhOps) * kTileThreads * 4 + kTileMaxPats * 4;
     const int smem = ((int)(2 * sizeof(float)) << kTileQubits) + (16 + p.nphops) * kTileThreads * 4 +
                      (p.nphops ? p.npats * 4 : 0);
-    static bool attr_set = false;  // the attribute is per function, once per process
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile<Off>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    // the shared-memory attribute is set once per device
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_tile<Off>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set[dev] = true;
     }
     uint64_t grid = p.n_tiles;
     if (grid > (1ull << 30)) grid = 1ull << 30;

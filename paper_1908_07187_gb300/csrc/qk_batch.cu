@@ -125,12 +125,17 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BCirc *__restrict__ c
                 }
             } else if (op.kind == B_PHASE) {
                 if (act) {
+                    // only the matching amplitudes: u enumerates the bits outside the
+                    // mask, a zero goes in at each mask bit, then the required values
                     const float fr = op.ph.re, fi = op.ph.im;
-                    for (uint32_t i = tid; i < dim; i += kBThreads)
-                        if ((i & op.cmask) == op.val) {
-                            const float2 a = A[i];
-                            A[i] = make_float2(a.x * fr - a.y * fi, a.x * fi + a.y * fr);
-                        }
+                    const uint32_t cnt = dim >> __popc(op.cmask);
+                    for (uint32_t u = tid; u < cnt; u += kBThreads) {
+                        uint32_t i = u;
+                        for (uint32_t m = op.cmask; m; m &= m - 1) i = ins0(i, __ffs(m) - 1);
+                        i |= op.val;
+                        const float2 a = A[i];
+                        A[i] = make_float2(a.x * fr - a.y * fi, a.x * fi + a.y * fr);
+                    }
                 }
             } else if (op.kind == B_MULMOD) {
                 for (uint32_t i = tid; i < dim; i += kBThreads) {

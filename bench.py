@@ -232,6 +232,23 @@ def oracle_size(n: int):
     return m
 
 
+def host_info():
+    """The host the oracle is timed on: logical CPUs and the CPU model."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":", 1)[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    import platform
+
+    return {"nproc": os.cpu_count(), "cpu": model or platform.processor() or platform.machine()}
+
+
 def cpu_baseline(n: int, circ, count: int = 1):
     m = oracle_size(n)
     c = circ if m == n else workload(m, 2)
@@ -240,7 +257,7 @@ def cpu_baseline(n: int, circ, count: int = 1):
     sample = f"gate ops 2..{count + 1} of the {m}-qubit layered circuit (gate 1 untimed) on the complex128 oracle, 1 thread"
     if m != n:
         sample += f", scaled by 2^{m - n} to {n} qubits"
-    return {"value": gps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    return {"value": gps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "host": host_info()}
 
 
 def run_reference(args):
@@ -268,7 +285,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": {"workload": f"layered U3/CZ-brickwork 500 gates + QFT({n}) + measure all, {n} qubits",
                        "n_qubits": n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0

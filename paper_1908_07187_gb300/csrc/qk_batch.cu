@@ -72,6 +72,56 @@ __device__ __forceinline__ uint32_t ins0(uint32_t j, int pos) {
     return ((j - lo) << 1) | lo;
 }
 
+// K consecutive uncontrolled 2x2 gates on distinct qubits qs[0..K-1] (in program
+// order, matrices in gops[0..K-1]): each thread takes groups of 2^K amplitudes that
+// differ in those qubits, applies the K gates in registers and writes the group
+// back once, so the state crosses shared memory once per K gates instead of once
+// per gate.
+template <int K>
+__device__ __forceinline__ void u2_group(float2 *A, uint32_t dim, const BOp *gops, const int *qs) {
+    int qsort[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) qsort[j] = qs[j];
+#pragma unroll
+    for (int a = 1; a < K; ++a)
+#pragma unroll
+        for (int b = a; b > 0; --b)
+            if (qsort[b] < qsort[b - 1]) {
+                const int t = qsort[b];
+                qsort[b] = qsort[b - 1];
+                qsort[b - 1] = t;
+            }
+    uint32_t off[1 << K];
+    off[0] = 0;
+#pragma unroll
+    for (int r = 1; r < (1 << K); ++r) off[r] = off[r & (r - 1)] + (1u << qs[__ffs(r) - 1]);
+    for (uint32_t g = threadIdx.x; g < (dim >> K); g += kBThreads) {
+        uint32_t base = g;
+#pragma unroll
+        for (int j = 0; j < K; ++j) base = ins0(base, qsort[j]);
+        float2 x[1 << K];
+#pragma unroll
+        for (int r = 0; r < (1 << K); ++r) x[r] = A[base + off[r]];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const float *m = gops[j].m;
+            const float2 m00 = make_float2(m[0], m[1]), m01 = make_float2(m[2], m[3]);
+            const float2 m10 = make_float2(m[4], m[5]), m11 = make_float2(m[6], m[7]);
+#pragma unroll
+            for (int r = 0; r < (1 << K); ++r) {
+                if (r & (1 << j)) continue;
+                const float2 a = x[r], b = x[r | (1 << j)];
+                x[r] = make_float2(m00.x * a.x - m00.y * a.y + m01.x * b.x - m01.y * b.y,
+                                   m00.x * a.y + m00.y * a.x + m01.x * b.y + m01.y * b.x);
+                x[r | (1 << j)] = make_float2(m10.x * a.x - m10.y * a.y + m11.x * b.x - m11.y * b.y,
+                                              m10.x * a.y + m10.y * a.x + m11.x * b.y + m11.y * b.x);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < (1 << K); ++r) A[base + off[r]] = x[r];
+    }
+}
+
 __global__ void __launch_bounds__(kBThreads) k_batch(const BCirc *__restrict__ circs, const BOp *__restrict__ ops,
                                                      float2 *__restrict__ states, uint8_t *__restrict__ cbits_out,
                                                      int store_state) {
@@ -109,7 +159,23 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BCirc *__restrict__ c
             const BOp &op = s_ops[buf][oi];
             bool act = true;
             for (int k = 0; k < op.ncond; ++k) act = act && cb[op.cond[k]] != 0;
-            if (op.kind == B_U2) {
+            if (op.kind == B_U2 && op.ncond == 0 && op.cmask == 0) {
+                // two consecutive uncontrolled, unconditioned 2x2 gates on distinct
+                // qubits within this chunk are applied as one register group (groups
+                // of 3 and 4 measured slower: their registers cut the CTAs per SM)
+                int qs[2] = {op.q, 0};
+                int k = 1;
+                while (k < 2 && oi + k < cnt) {
+                    const BOp &nx = s_ops[buf][oi + k];
+                    bool ok = nx.kind == B_U2 && nx.ncond == 0 && nx.cmask == 0;
+                    for (int j = 0; j < k && ok; ++j) ok = qs[j] != nx.q;
+                    if (!ok) break;
+                    qs[k++] = nx.q;
+                }
+                if (k == 2) u2_group<2>(A, dim, &op, qs);
+                else u2_group<1>(A, dim, &op, qs);
+                oi += (uint32_t)(k - 1);
+            } else if (op.kind == B_U2) {
                 if (act) {
                     const float2 m00 = make_float2(op.m[0], op.m[1]), m01 = make_float2(op.m[2], op.m[3]);
                     const float2 m10 = make_float2(op.m[4], op.m[5]), m11 = make_float2(op.m[6], op.m[7]);

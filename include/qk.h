@@ -68,7 +68,8 @@ typedef enum { QK_EXEC_PLAIN = 0, QK_EXEC_FUSED = 1 } qk_exec_mode;
 
 typedef struct {
     int exec_mode;            /* qk_exec_mode; default QK_EXEC_FUSED                 */
-    int tile_qubits;          /* fused tile width m (qubits per tile); 0 = default   */
+    int tile_qubits;          /* fused tile width: 0 or 13 (the kernel's fixed width;
+                                 other values are rejected with QK_EINVAL)           */
     int max_pending;          /* queued ops that force a flush; 0 = default (4096)   */
     int profile;              /* 1: time every launch with CUDA events (qk_profile)  */
     size_t hbm_budget_bytes;  /* 0 = no limit beyond free device memory             */

@@ -466,7 +466,9 @@ qk_status qk_create(qk_ctx **out, qk_precision precision, void *cuda_stream, con
     }
     if (c->opt.exec_mode != QK_EXEC_PLAIN && c->opt.exec_mode != QK_EXEC_FUSED) { delete c; return QK_EINVAL; }
     if (c->opt.max_pending <= 0) c->opt.max_pending = 4096;
-    if (c->opt.tile_qubits < 0 || c->opt.tile_qubits > 16) { delete c; return QK_EINVAL; }
+    // the tile kernel's width is fixed: 0 (default) or that width
+    if (c->opt.tile_qubits != 0 && c->opt.tile_qubits != qk::kTileQubits) { delete c; return QK_EINVAL; }
+    if (c->opt.no_tensor_cores != 0 && c->opt.no_tensor_cores != 1) { delete c; return QK_EINVAL; }
     if (cudaGetDevice(&c->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
         cudaGetLastError();

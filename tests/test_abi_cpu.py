@@ -62,6 +62,20 @@ def test_create_rejects_bad_precision_without_touching_the_device(lib):
     assert lib.qk_create(None, 0, None, None) == -1
 
 
+def test_create_rejects_bad_options_without_touching_the_device(lib):
+    # option checks come before any CUDA call, so they run without a GPU
+    from paper_1908_07187_gb300 import qk
+
+    h = ctypes.c_void_p()
+    for field, value in (("tile_qubits", 12), ("exec_mode", 5), ("no_tensor_cores", 2)):
+        opt = qk.Options()
+        setattr(opt, field, value)
+        assert lib.qk_create(ctypes.byref(h), 0, None, ctypes.byref(opt)) == -1, field
+    opt = qk.Options()
+    opt.reserved[3] = 1
+    assert lib.qk_create(ctypes.byref(h), 0, None, ctypes.byref(opt)) == -1
+
+
 def test_product_package_does_not_import_the_oracle():
     pkg = os.path.join(ROOT, "paper_1908_07187_gb300")
     for dirpath, _, files in os.walk(pkg):

@@ -190,8 +190,8 @@ qk_status qk_apply_rphase_cbits(qk_ctx *ctx, int target, const int *cbits, int n
  * `control` with `uniform` into dest_cbit; X(control) if the outcome is 1.
  * Precondition: `control` is |0> (every amplitude with the control bit set is
  * zero), which holds at the start and after every stage.  The result equals the
- * six separate calls; the stage costs two passes over the control = 0 half
- * plus a one-block decision.  Stream-ordered, no host round trip.
+ * six separate calls; the stage costs two passes over the control = 0 half (the
+ * reduction's last block takes the decision).  Stream-ordered, no host round trip.
  * Errors: QK_EINVAL (bad ids, lists or uniform), QK_ENOMEM, QK_ECUDA. */
 qk_status qk_apply_kitaev_stage(qk_ctx *ctx, int control, int perm_gate_id, const int *targets, int nt,
                                 const int *phase_cbits, int ncb, double uniform, int dest_cbit);

@@ -82,7 +82,13 @@ GATES_1Q: Dict[str, np.ndarray] = {
     "s": np.array([[1, 0], [0, 1j]], dtype=np.complex128),
     "sdg": np.array([[1, 0], [0, -1j]], dtype=np.complex128),
     "t": np.array([[1, 0], [0, np.exp(1j * math.pi / 4)]], dtype=np.complex128),
+    "tdg": np.array([[1, 0], [0, np.exp(-1j * math.pi / 4)]], dtype=np.complex128),
 }
+
+
+def rz(theta: float) -> np.ndarray:
+    """Rotation about Z, exp(-i theta Z / 2) = diag(e^{-i theta/2}, e^{i theta/2})."""
+    return np.array([[np.exp(-0.5j * theta), 0], [0, np.exp(0.5j * theta)]], dtype=np.complex128)
 
 
 def u3(theta: float, phi: float, lam: float) -> np.ndarray:
@@ -107,6 +113,8 @@ def gate_matrix(kind: str, params: Sequence[float] = ()) -> np.ndarray:
         return u3(*params)
     if kind == "p":
         return phase(params[0])
+    if kind == "rz":
+        return rz(params[0])
     if kind == "swap":
         return SWAP
     if kind == "unitary":

@@ -26,16 +26,19 @@ def requests(count, seed0=100, n_max=13):
     return [workloads.serving_request(seed0 + i, n_min=3, n_max=n_max) for i in range(count)]
 
 
-def oracle_margins_ok(circ, ref):
-    """True when no measured uniform lies within MARGIN of its P0."""
+def oracle_margin(circ):
+    """Smallest |u - P0| over every measured qubit of the circuit, each taken in
+    list order on the oracle's state at that point."""
     st = oracle.OracleState(circ.n_qubits, circ.n_cbits)
+    margin = 1.0
     for op in circ.ops:
         if op.kind == "measure":
-            p0 = st.prob0(op.targets[0])
-            if abs(op.uniforms[0] - p0) < MARGIN:
-                return False
+            for j, (q, u) in enumerate(zip(op.targets, op.uniforms)):
+                margin = min(margin, abs(u - st.prob0(q)))
+                st.measure([q], [u], [op.cbits[j]] if op.cbits else ())
+            continue
         st.apply_op(op)
-    return True
+    return margin
 
 
 def test_batch_matches_oracle_and_engine(qk):
@@ -44,10 +47,15 @@ def test_batch_matches_oracle_and_engine(qk):
     for c in reqs:
         b.add_ops(c.n_qubits, c.n_cbits, c.ops)
     b.run()
+    near_ties = []
     for i, c in enumerate(reqs):
         bits, psi = b.read(i)
         ref = oracle.run_circuit(c)
-        if not oracle_margins_ok(c, ref):
+        if oracle_margin(c) < MARGIN:
+            # a uniform within the complex64 bound of P0 may go either way: such a
+            # circuit is reported, and only its bits' validity is checked
+            near_ties.append(c.name)
+            assert all(x in (0, 1) for x in bits)
             continue
         assert list(bits) == [int(x) for x in ref.cbits], c.name
         assert np.max(np.abs(psi.astype(np.complex128) - ref.psi)) < 1e-4, c.name
@@ -55,6 +63,8 @@ def test_batch_matches_oracle_and_engine(qk):
         assert list(ctx.read_cbits()) == list(bits), c.name
         ctx.close()
     b.close()
+    # with 40 circuits and a 1e-6 margin a near tie is a rare event (about 1e-4)
+    assert len(near_ties) <= 1, near_ties
 
 
 def test_batch_result_is_the_same_alone_and_in_the_mix(qk):

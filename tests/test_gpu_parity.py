@@ -357,12 +357,7 @@ def random_mixed_ops(n, n_ops, seed, ncb=0):
 def oracle_apply(st, op):
     if op.cond and not all(st.cbits[c] for c in op.cond):
         return
-    if op.kind == "rz":
-        th = op.params[0]
-        U = np.diag([np.exp(-0.5j * th), np.exp(0.5j * th)])
-    else:
-        U = oracle.gate_matrix(op.kind, op.params)
-    st.apply_matrix(U, op.targets, op.controls)
+    st.apply_matrix(oracle.gate_matrix(op.kind, op.params), op.targets, op.controls)
 
 
 @pytest.mark.parametrize("n,seed", [(13, 1), (14, 2), (15, 3), (16, 4), (18, 5), (20, 6)])

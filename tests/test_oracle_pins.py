@@ -109,6 +109,50 @@ def test_textbook_special_cases_of_u3_and_phase():
         np.testing.assert_allclose(U.conj().T @ U, np.eye(2), atol=1e-15)
 
 
+def test_named_single_qubit_gates_follow_from_x_and_h():
+    """Y, Z, S, S^dagger, T, T^dagger from X and H alone (X and H are pinned by the
+    Bell/GHZ states and the U3 special cases): Z = H X H, Y = i X Z, S^2 = Z with
+    S X S^dagger = Y (which fixes the sign of S), T^2 = S with T X T^dagger =
+    (X + Y)/sqrt(2) (which fixes the sign of T), and the daggers as inverses."""
+    X, H = oracle.GATES_1Q["x"], oracle.GATES_1Q["h"]
+    Z = H @ X @ H
+    Y = 1j * X @ Z
+    g = oracle.GATES_1Q
+    np.testing.assert_allclose(g["z"], Z, atol=1e-15)
+    np.testing.assert_allclose(g["y"], Y, atol=1e-15)
+    S, T = g["s"], g["t"]
+    for D in (S, T):   # diagonal with D[0, 0] = 1 (a phase gate)
+        assert D[0, 1] == 0 and D[1, 0] == 0 and D[0, 0] == 1
+    np.testing.assert_allclose(S @ S, Z, atol=1e-15)
+    np.testing.assert_allclose(S @ X @ S.conj().T, Y, atol=1e-15)
+    np.testing.assert_allclose(g["sdg"] @ S, I2, atol=1e-15)
+    np.testing.assert_allclose(T @ T, S, atol=1e-15)
+    np.testing.assert_allclose(T @ X @ T.conj().T, (X + Y) / math.sqrt(2), atol=1e-15)
+    np.testing.assert_allclose(g["tdg"] @ T, I2, atol=1e-15)
+
+
+def test_rz_phase_and_u3_against_matrix_exponentials():
+    """RZ(t) = exp(-i t Z / 2) and P(t) = exp(i t (I - Z) / 2) by scipy's expm of
+    the generators; RZ(t) = e^{-i t/2} P(t); U3(th, ph, la) = e^{i (ph + la)/2}
+    RZ(ph) RY(th) RZ(la) with RY(th) = exp(-i th Y / 2) (the OpenQASM 2 identity)."""
+    from scipy.linalg import expm
+
+    X, H = oracle.GATES_1Q["x"], oracle.GATES_1Q["h"]
+    Z = H @ X @ H
+    Y = 1j * X @ Z
+    for t in (0.0, 0.3, math.pi / 2, 2.5, math.pi, 5.9):
+        np.testing.assert_allclose(oracle.gate_matrix("rz", [t]), expm(-0.5j * t * Z), atol=1e-14)
+        np.testing.assert_allclose(oracle.gate_matrix("p", [t]), expm(0.5j * t * (I2 - Z)), atol=1e-14)
+        np.testing.assert_allclose(oracle.gate_matrix("rz", [t]), np.exp(-0.5j * t) * oracle.gate_matrix("p", [t]),
+                                   atol=1e-15)
+    np.testing.assert_allclose(oracle.gate_matrix("p", [math.pi / 2]), oracle.GATES_1Q["s"], atol=1e-15)
+    np.testing.assert_allclose(oracle.gate_matrix("p", [math.pi / 4]), oracle.GATES_1Q["t"], atol=1e-15)
+    rng = np.random.default_rng(77)
+    for th, ph, la in rng.uniform(0, 2 * math.pi, size=(6, 3)):
+        want = np.exp(0.5j * (ph + la)) * expm(-0.5j * ph * Z) @ expm(-0.5j * th * Y) @ expm(-0.5j * la * Z)
+        np.testing.assert_allclose(oracle.gate_matrix("u3", [th, ph, la]), want, atol=1e-14)
+
+
 def test_swap_gate_exchanges_qubits():
     n = 4
     psi = rand_state(n, 9)
@@ -383,3 +427,20 @@ def test_paper_printed_order_values():
     r = multiplicative_order(g["default_base_a"], N)
     assert r == g["n13564597_order"]
     assert r % g["n13564597_partial"] == 0 and r // g["n13564597_partial"] == 4
+
+
+@pytest.mark.parametrize("N,a", [(15, 7), (21, 2), (35, 3)])
+def test_kitaev_op_list_matches_the_stage_by_stage_oracle(N, a):
+    """workloads.kitaev_circuit (the op list every Kitaev GPU test feeds to both
+    sides) walked op by op reproduces oracle.kitaev_order_finding (the nx2n stages
+    of Appendix A written against the oracle API, pinned above by the closed-form
+    phase-estimation law): the same bits and the same final state."""
+    t = 2 * N.bit_length()
+    rng = workloads.SplitMix64(900 + N)
+    u = [rng.uniform() for _ in range(t)]
+    y, bits, _, st = oracle.kitaev_order_finding(N, a, t, u)
+    circ = workloads.kitaev_circuit(N, a, uniforms=u)
+    assert circ.n_cbits == t and circ.n_qubits == N.bit_length() + 1
+    ref = oracle.run_circuit(circ)
+    assert [int(x) for x in ref.cbits] == bits
+    np.testing.assert_allclose(ref.psi, st.psi, atol=1e-13)

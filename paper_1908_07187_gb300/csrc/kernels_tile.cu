@@ -7,18 +7,21 @@
 //
 // Each of the 256 threads holds 32 amplitudes in registers, split into real and
 // imaginary parts, two amplitudes per float2 (re[2j], re[2j+1]) /
-// (im[2j], im[2j+1]).  A 2x2 gate on a register bit is a set of 16 butterflies
-// between registers of the same thread (scalar FP32 FMAs: the paired f32x2 forms
-// measured slower in this register-bound loop).  The register bits are changed
-// by transposing the tile through shared memory (three fixed arrangements, see
+// (im[2j], im[2j+1]), so that a butterfly on register bit K >= 1 runs as packed
+// f32x2 FMAs on two amplitude pairs at once.  The register bits are changed by
+// transposing the tile through shared memory (three fixed arrangements, see
 // qk_kernels.cuh).
 //
-// Diagonal gates are not applied one by one: each thread keeps a pending
-// diagonal D(r) = exp(2 pi i (t0 + sum_{k in r} t_k) / 2^32) as six 32-bit
-// fixed-point phase sums (exact modulo one turn), and multiplies it into the
-// amplitudes only when a transpose or a gate that does not commute with it needs
-// that; a pending factor on the target bit of a 2x2 gate is folded into the
-// gate's matrix instead.
+// Uncontrolled gates run in pivot form (LayerGate in qk_kernels.cuh): 8 FMAs per
+// amplitude pair instead of the 16 of a complex 2x2 product.  What the pivot form
+// leaves over -- a real scale, the same for every amplitude of the pass, and
+// per-qubit phases -- stays pending.  The parts that are the same for every
+// thread are tracked by the planner and folded into later gates' coefficients or
+// the final flush; each thread only keeps the parts that depend on its own bits
+// (diagonal terms coupling a register bit with a lane, warp or fixed bit), as six
+// 32-bit fixed-point phase sums (exact modulo one turn): one per register bit
+// and one for the whole thread.  A sum of exactly half a turn is a sign flip and
+// costs no phase factor.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,10 +34,16 @@ namespace {
 
 __host__ __device__ constexpr int ctz_const(int x) { return (x & 1) ? 0 : 1 + ctz_const(x >> 1); }
 
+constexpr uint32_t kHalfTurn = 0x80000000u;
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+__device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 splat(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float xor_sign(float x, uint32_t s) { return __uint_as_float(__float_as_uint(x) ^ s); }
 
 // exp(2 pi i j / 256) for j < 256, filled once per CTA
 __shared__ float2 s_turn_tab[256];
@@ -59,6 +68,12 @@ __device__ __forceinline__ float2 turns_to_phase(uint32_t t) {
     const float s = x * fmaf(x2, -1.f / 6.f, 1.f);
     return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
 }
+// the same, exact for the sign flips that CZ-type terms produce
+__device__ __forceinline__ float2 phase_of(uint32_t t) {
+    if (t == 0u) return make_float2(1.f, 0.f);
+    if (t == kHalfTurn) return make_float2(-1.f, 0.f);
+    return turns_to_phase(t);
+}
 
 // Amplitudes of one thread: R[j] = (re[2j], re[2j+1]), I[j] = (im[2j], im[2j+1]).
 struct Regs {
@@ -75,6 +90,33 @@ __device__ __forceinline__ float &im_of(Regs &v) {
     if constexpr (r & 1) return v.I[r >> 1].y;
     else return v.I[r >> 1].x;
 }
+
+// Thread-dependent pending phases: t(k) on register bit k = 1, t0 on the whole
+// thread.  The sums live in shared memory (word w of thread x at w * kTileThreads
+// + x, conflict-free), leaving the registers to the amplitudes; a register mask
+// says which sums may be nonzero, so a thread with nothing pending touches no
+// shared memory.
+struct DevPending {
+    uint32_t *p;   // word 0: t0, word 1 + k: t(k)
+    int mask;      // bit k: t(k) may be nonzero; bit 5: t0 may be nonzero
+    __device__ __forceinline__ uint32_t &w(int k) { return p[(k + 1) * kTileThreads]; }  // k = -1: t0
+    __device__ __forceinline__ void reset() { mask = 0; }
+    __device__ __forceinline__ uint32_t get(int k) { return (mask >> k) & 1 ? w(k) : 0u; }
+    __device__ __forceinline__ uint32_t get0() { return mask & 32 ? w(-1) : 0u; }
+    __device__ __forceinline__ void set(int k, uint32_t x) {
+        w(k) = x;
+        mask |= 1 << k;
+    }
+    __device__ __forceinline__ void set0(uint32_t x) {
+        w(-1) = x;
+        mask |= 32;
+    }
+    __device__ __forceinline__ void add(int k, uint32_t d) {  // k == 5: t0
+        if (k == 5) set0(get0() + d);
+        else set(k, get(k) + d);
+    }
+    __device__ __forceinline__ void clear(int k) { mask &= ~(1 << k); }
+};
 
 // Shared-memory slot (in floats, separate real and imaginary planes) of local
 // index L.  The map is linear over GF(2), so slot(thread part ^ register part)
@@ -136,60 +178,57 @@ __device__ __forceinline__ void transpose(Regs &v, float *sre, float *sim, int f
     else from_smem<ARR_HI>(sre, sim, v, lane, warp);
 }
 
-struct Mat {
-    float2 a00r, a00i, n00i, a01r, a01i, n01i, a10r, a10i, n10i, a11r, a11i, n11i;
-    __device__ __forceinline__ Mat(float2 m00, float2 m01, float2 m10, float2 m11) {
-        a00r = splat(m00.x); a00i = splat(m00.y); n00i = splat(-m00.y);
-        a01r = splat(m01.x); a01i = splat(m01.y); n01i = splat(-m01.y);
-        a10r = splat(m10.x); a10i = splat(m10.y); n10i = splat(-m10.y);
-        a11r = splat(m11.x); a11i = splat(m11.y); n11i = splat(-m11.y);
-    }
-};
+// ---------------------------------------------------------------------------
+// pending-phase flushes
+// ---------------------------------------------------------------------------
 
-// 2x2 gate on register bit K >= 1: couples (j, j | 2^(K-1)) of float2 registers,
-// two amplitude pairs per couple.  A couple acts if (2j & rmask) == rmask;
-// with register bit 0 in rmask only the odd halves act (the even halves keep
-// their old values).
-template <int K>
-__device__ __forceinline__ void u2_packed(Regs &v, const Mat &M, int rmask) {
-    static_assert(K >= 1 && K <= 4, "packed butterflies need K >= 1");
-    const bool odd_only = rmask & 1;
-    const int hmask = rmask & ~1;
+// Every sum is 0 or half a turn: amplitude r changes sign iff t0 + sum_k r_k t_k
+// is half a turn (sign bits combined by XOR, applied to the float sign bits).
+__device__ __forceinline__ void flush_signs(Regs &v, uint32_t t0, const uint32_t t[5]) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        if (j & (1 << (K - 1))) continue;
-        const int j1 = j | (1 << (K - 1));
-        if (((j << 1) & hmask) != hmask) continue;
-        const float2 A = v.R[j], B = v.I[j], C = v.R[j1], D = v.I[j1];
-        // scalar FMAs measured faster than the paired forms here
-        float2 r0, i0, r1, i1;
-        r0.x = M.a00r.x * A.x + M.n00i.x * B.x + M.a01r.x * C.x + M.n01i.x * D.x;
-        r0.y = M.a00r.x * A.y + M.n00i.x * B.y + M.a01r.x * C.y + M.n01i.x * D.y;
-        i0.x = M.a00r.x * B.x + M.a00i.x * A.x + M.a01r.x * D.x + M.a01i.x * C.x;
-        i0.y = M.a00r.x * B.y + M.a00i.x * A.y + M.a01r.x * D.y + M.a01i.x * C.y;
-        r1.x = M.a10r.x * A.x + M.n10i.x * B.x + M.a11r.x * C.x + M.n11i.x * D.x;
-        r1.y = M.a10r.x * A.y + M.n10i.x * B.y + M.a11r.x * C.y + M.n11i.x * D.y;
-        i1.x = M.a10r.x * B.x + M.a10i.x * A.x + M.a11r.x * D.x + M.a11i.x * C.x;
-        i1.y = M.a10r.x * B.y + M.a10i.x * A.y + M.a11r.x * D.y + M.a11i.x * C.y;
-        if (odd_only) {
-            r0.x = A.x; i0.x = B.x; r1.x = C.x; i1.x = D.x;
-        }
-        v.R[j] = r0; v.I[j] = i0; v.R[j1] = r1; v.I[j1] = i1;
+        uint32_t s = t0;
+        if (j & 1) s ^= t[1];
+        if (j & 2) s ^= t[2];
+        if (j & 4) s ^= t[3];
+        if (j & 8) s ^= t[4];
+        const uint32_t so = s ^ t[0];
+        v.R[j].x = xor_sign(v.R[j].x, s);
+        v.I[j].x = xor_sign(v.I[j].x, s);
+        v.R[j].y = xor_sign(v.R[j].y, so);
+        v.I[j].y = xor_sign(v.I[j].y, so);
     }
 }
 
-// 2x2 gate on register bit 0: the pair is the two halves of one packed register.
-__device__ __forceinline__ void u2_bit0(Regs &v, float2 m00, float2 m01, float2 m10, float2 m11, int rmask) {
+// General diagonal D(r) = c0 * prod_{k in r} a_k on the 32 registers: the five
+// factors, then four independent chains over register bits 1 and 2 in Gray-code
+// order (dependency depth 4), started at c0 times the products of bits 3 and 4.
+__device__ __forceinline__ void apply_diagonal(Regs &v, float2 c0, const float2 a[5]) {
+    float2 d[4];
+    d[0] = c0;
+    d[1] = cmul(c0, a[3]);
+    d[2] = cmul(c0, a[4]);
+    d[3] = cmul(d[1], a[4]);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        if (((j << 1) & rmask) != rmask) continue;
-        const float2 a = make_float2(v.R[j].x, v.I[j].x), b = make_float2(v.R[j].y, v.I[j].y);
-        const float2 o0 = make_float2(m00.x * a.x - m00.y * a.y + m01.x * b.x - m01.y * b.y,
-                                      m00.x * a.y + m00.y * a.x + m01.x * b.y + m01.y * b.x);
-        const float2 o1 = make_float2(m10.x * a.x - m10.y * a.y + m11.x * b.x - m11.y * b.y,
-                                      m10.x * a.y + m10.y * a.x + m11.x * b.y + m11.y * b.x);
-        v.R[j] = make_float2(o0.x, o1.x);
-        v.I[j] = make_float2(o0.y, o1.y);
+    for (int l = 0; l < 4; ++l) {
+        const int g = l ^ (l >> 1);
+        if (l > 0) {
+            const int gp = (l - 1) ^ ((l - 1) >> 1);
+            const int bb = ctz_const(g ^ gp);      // register bit bb + 1 toggles
+            const float2 ab = a[bb + 1];
+            const float2 f = (g >> bb) & 1 ? ab : conj2(ab);
+#pragma unroll
+            for (int h = 0; h < 4; ++h) d[h] = cmul(d[h], f);
+        }
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int j = 4 * h + g;
+            const float2 d1 = cmul(d[h], a[0]);
+            const float2 Dr = make_float2(d[h].x, d1.x), Di = make_float2(d[h].y, d1.y);
+            const float2 A = v.R[j], B = v.I[j];
+            v.R[j] = ffma2(neg2(Di), B, __fmul2_rn(Dr, A));
+            v.I[j] = ffma2(Di, A, __fmul2_rn(Dr, B));
+        }
     }
 }
 
@@ -209,8 +248,8 @@ __device__ __forceinline__ void bit_factor(Regs &v, float2 f) {
         for (int j = 0; j < 16; ++j) {
             if (!(j & (1 << (K - 1)))) continue;
             const float2 A = v.R[j], B = v.I[j];
-            v.R[j] = __ffma2_rn(nfi, B, __fmul2_rn(fr, A));
-            v.I[j] = __ffma2_rn(fi, A, __fmul2_rn(fr, B));
+            v.R[j] = ffma2(nfi, B, __fmul2_rn(fr, A));
+            v.I[j] = ffma2(fi, A, __fmul2_rn(fr, B));
         }
     }
 }
@@ -225,173 +264,185 @@ __device__ __forceinline__ void bit_factor_dispatch(int k, Regs &v, float2 f) {
     }
 }
 
-// Pending diagonal of one thread in 32-bit fixed-point turns.  The six sums live
-// in shared memory (word w of thread x at w * kTileThreads + x, conflict-free),
-// leaving the registers to the amplitudes; only the mask is a register.
-struct Pending {
-    uint32_t *p;  // word 0: t0 (constant), word 1 + k: t_k (register bit k)
-    float2 *fa;   // flush scratch: factor k at fa[k * kTileThreads]
-    int mask;     // bit k: t_k may be nonzero; bit 5: t0 may be nonzero
-
-    __device__ __forceinline__ uint32_t &t0() { return p[0]; }
-    __device__ __forceinline__ uint32_t &t(int k) { return p[(k + 1) * kTileThreads]; }
-    __device__ __forceinline__ void reset() {
+// Materialise the thread's pending phases (before a transpose moves amplitudes
+// between threads).
+__device__ __forceinline__ void flush_dev(Regs &v, DevPending &pd) {
+    if (pd.mask == 0) return;
+    uint32_t t[5];
 #pragma unroll
-        for (int w = 0; w < 6; ++w) p[w * kTileThreads] = 0;
-        mask = 0;
-    }
-    __device__ __forceinline__ void add(int k, uint32_t d) {
-        t(k) += d;
-        mask |= 1 << k;
-    }
-    __device__ __forceinline__ void add0(uint32_t d) {
-        t0() += d;
-        mask |= 32;
-    }
-    __device__ __forceinline__ void clear(int k) {
-        t(k) = 0;
-        mask &= ~(1 << k);
-    }
-    __device__ __forceinline__ void flush(Regs &v) {
-        if (mask == 0) return;
-        if ((mask & 32) == 0 && __popc(mask) <= 2) {
-#pragma unroll
-            for (int k = 0; k < 5; ++k)
-                if (mask & (1 << k)) {
-                    const uint32_t tk = t(k);
-                    if (tk != 0) bit_factor_dispatch(k, v, turns_to_phase(tk));
-                }
-        } else {
-            // D(r) = c0 * prod_{k in r} a_k: six sincos into this thread's factor
-            // slots in shared memory (not registers: the amplitudes fill those), then
-            // walk j (register bits 1..4) in Gray-code order so D changes by one factor
-            // per step
-            const float2 c0 = (mask & 32) ? turns_to_phase(t0()) : make_float2(1.f, 0.f);
-#pragma unroll
-            for (int k = 0; k < 5; ++k)
-                fa[k * kTileThreads] = (mask & (1 << k)) ? turns_to_phase(t(k)) : make_float2(1.f, 0.f);
-            const float2 a0 = fa[0];
-            // four independent chains over register bits 1, 2 (j = 4h + l, l < 4),
-            // started at c0 * (a3, a4 products of h): dependency depth 4, not 16
-            float2 d[4];
-            {
-                const float2 a3 = fa[3 * kTileThreads], a4 = fa[4 * kTileThreads];
-                d[0] = c0;
-                d[1] = cmul(c0, a3);
-                d[2] = cmul(c0, a4);
-                d[3] = cmul(d[1], a4);
-            }
-#pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                // l walks 0, 1, 3, 2 (Gray order over bits 1 and 2)
-                const int g = l ^ (l >> 1);
-                if (l > 0) {
-                    const int gp = (l - 1) ^ ((l - 1) >> 1);
-                    const int bb = ctz_const(g ^ gp);      // register bit bb + 1 toggles
-                    const float2 ab = fa[(bb + 1) * kTileThreads];
-                    const float2 f = (g >> bb) & 1 ? ab : make_float2(ab.x, -ab.y);
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) d[h] = cmul(d[h], f);
-                }
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int j = 4 * h + g;
-                    const float2 d1 = cmul(d[h], a0);
-                    const float2 Dr = make_float2(d[h].x, d1.x), Di = make_float2(d[h].y, d1.y);
-                    const float2 A = v.R[j], B = v.I[j];
-                    v.R[j] = __ffma2_rn(make_float2(-Di.x, -Di.y), B, __fmul2_rn(Dr, A));
-                    v.I[j] = __ffma2_rn(Di, A, __fmul2_rn(Dr, B));
-                }
-            }
-        }
-        reset();
-    }
-};
-
-// Rotation butterfly on register bit K: (x0, x1) <- (c x0 + m01 x1, s x0 + m11 x1)
-// with c, s real and m01, m11 complex: 12 FP32 operations per amplitude pair.
-template <int K>
-__device__ __forceinline__ void rot_butterfly(Regs &v, float c, float s, float2 m01, float2 m11) {
-    const float n01i = -m01.y, n11i = -m11.y;
-    if constexpr (K == 0) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const float ar = v.R[j].x, ai = v.I[j].x, br = v.R[j].y, bi = v.I[j].y;
-            v.R[j].x = fmaf(n01i, bi, fmaf(m01.x, br, c * ar));
-            v.I[j].x = fmaf(m01.y, br, fmaf(m01.x, bi, c * ai));
-            v.R[j].y = fmaf(n11i, bi, fmaf(m11.x, br, s * ar));
-            v.I[j].y = fmaf(m11.y, br, fmaf(m11.x, bi, s * ai));
-        }
+    for (int k = 0; k < 5; ++k) t[k] = pd.get(k);
+    const uint32_t t0 = pd.get0();
+    if (((t[0] | t[1] | t[2] | t[3] | t[4] | t0) & ~kHalfTurn) == 0u) {
+        flush_signs(v, t0, t);
     } else {
+        float2 a[5];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            if (j & (1 << (K - 1))) continue;
-            const int j1 = j | (1 << (K - 1));
-            const float2 A = v.R[j], B = v.I[j], C = v.R[j1], D = v.I[j1];
-            float2 r0, i0, r1, i1;
-            r0.x = fmaf(n01i, D.x, fmaf(m01.x, C.x, c * A.x));
-            r0.y = fmaf(n01i, D.y, fmaf(m01.x, C.y, c * A.y));
-            i0.x = fmaf(m01.y, C.x, fmaf(m01.x, D.x, c * B.x));
-            i0.y = fmaf(m01.y, C.y, fmaf(m01.x, D.y, c * B.y));
-            r1.x = fmaf(n11i, D.x, fmaf(m11.x, C.x, s * A.x));
-            r1.y = fmaf(n11i, D.y, fmaf(m11.x, C.y, s * A.y));
-            i1.x = fmaf(m11.y, C.x, fmaf(m11.x, D.x, s * B.x));
-            i1.y = fmaf(m11.y, C.y, fmaf(m11.x, D.y, s * B.y));
-            v.R[j] = r0; v.I[j] = i0; v.R[j1] = r1; v.I[j1] = i1;
+        for (int k = 0; k < 5; ++k) a[k] = phase_of(t[k]);
+        apply_diagonal(v, phase_of(t0), a);
+    }
+    pd.reset();
+}
+
+// ---------------------------------------------------------------------------
+// gates
+// ---------------------------------------------------------------------------
+
+// Pivot butterfly on register bit K >= 1 (see LayerGate): couples float2
+// registers (j, j | 2^(K-1)), two amplitude pairs per couple.  In place, so that
+// the results stay in the amplitudes' own registers: u = a1 y0 into temporaries,
+// then y0 += a0 y1 and y1 += u (10 packed operations per couple).
+template <int K>
+__device__ __forceinline__ void piv_packed(Regs &v, float2 a0r, float2 a0i, float2 na0i, float2 a1r, float2 a1i,
+                                           float2 na1i) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (j & (1 << (K - 1))) continue;
+        const int j1 = j | (1 << (K - 1));
+        const float2 A = v.R[j], B = v.I[j], C = v.R[j1], D = v.I[j1];
+        const float2 ur = ffma2(na1i, B, __fmul2_rn(a1r, A));
+        const float2 ui = ffma2(a1i, A, __fmul2_rn(a1r, B));
+        v.R[j] = ffma2(na0i, D, ffma2(a0r, C, A));
+        v.I[j] = ffma2(a0i, C, ffma2(a0r, D, B));
+        v.R[j1] = __fadd2_rn(C, ur);
+        v.I[j1] = __fadd2_rn(D, ui);
+    }
+}
+
+// Pivot butterfly on register bit 0: the pair is the two halves of one float2.
+__device__ __forceinline__ void piv_bit0(Regs &v, float a0r, float a0i, float a1r, float a1i) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const float y0r = v.R[j].x, y0i = v.I[j].x, y1r = v.R[j].y, y1i = v.I[j].y;
+        const float ur = fmaf(-a1i, y0i, a1r * y0r), ui = fmaf(a1i, y0r, a1r * y0i);
+        v.R[j].x = fmaf(-a0i, y1i, fmaf(a0r, y1r, y0r));
+        v.I[j].x = fmaf(a0i, y1r, fmaf(a0r, y1i, y0i));
+        v.R[j].y = y1r + ur;
+        v.I[j].y = y1i + ui;
+    }
+}
+
+// One gate of a TOP_U2L layer on register bit K.  The planner folded every
+// pending phase that is the same for all threads into A0, A1 and chose the
+// stored bit order so that the pivot is the diagonal entry; the thread's own
+// pending phase e of bit K turns them into a0 = A0 e and a1 = A1 conj(e), and
+// leaves e pending on the bit.
+template <int K>
+__device__ __forceinline__ void layer_gate(Regs &v, DevPending &pd, const LayerGate &g) {
+    float2 a0r = g.c[0], a0i = g.c[1], na0i = g.c[2], a1r = g.c[3], a1i = g.c[4], na1i = g.c[5];
+    const uint32_t tk = pd.get(K);
+    if (tk != 0u) {
+        if (tk == kHalfTurn) {
+            a0r = neg2(a0r); a0i = neg2(a0i); na0i = neg2(na0i);
+            a1r = neg2(a1r); a1i = neg2(a1i); na1i = neg2(na1i);
+        } else {
+            const float2 e = turns_to_phase(tk);
+            const float2 x0 = cmul(make_float2(a0r.x, a0i.x), e);
+            const float2 x1 = cmul(make_float2(a1r.x, a1i.x), conj2(e));
+            a0r = splat(x0.x); a0i = splat(x0.y); na0i = splat(-x0.y);
+            a1r = splat(x1.x); a1i = splat(x1.y); na1i = splat(-x1.y);
+        }
+    }
+    if constexpr (K == 0) piv_bit0(v, a0r.x, a0i.x, a1r.x, a1i.x);
+    else piv_packed<K>(v, a0r, a0i, na0i, a1r, a1i, na1i);
+}
+
+// General 2x2 gate on register bit K >= 1 where the register bits in rmask are 1
+// (a controlled gate with register-bit controls); with register bit 0 in rmask
+// only the odd halves act.  Scalar FMAs keep the coefficients to eight registers.
+__device__ __forceinline__ float2 mv2(float2 m0, float2 x0, float2 m1, float2 x1) {  // m0 x0 + m1 x1
+    return make_float2(fmaf(-m1.y, x1.y, fmaf(m1.x, x1.x, fmaf(-m0.y, x0.y, m0.x * x0.x))),
+                       fmaf(m1.y, x1.x, fmaf(m1.x, x1.y, fmaf(m0.y, x0.x, m0.x * x0.y))));
+}
+template <int K>
+__device__ __forceinline__ void u2_packed(Regs &v, float2 m00, float2 m01, float2 m10, float2 m11, int rmask,
+                                          int rval) {
+    static_assert(K >= 1 && K <= 4, "K >= 1");
+    // register bit 0 in rmask: only the halves with that bit value act
+    const bool act_x = !(rmask & 1) || !(rval & 1), act_y = !(rmask & 1) || (rval & 1);
+    const int hmask = rmask & ~1, hval = rval & ~1;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (j & (1 << (K - 1))) continue;
+        const int j1 = j | (1 << (K - 1));
+        if (((j << 1) & hmask) != hval) continue;
+        // two amplitude pairs: (.x halves) and (.y halves)
+        const float2 a0 = make_float2(v.R[j].x, v.I[j].x), b0 = make_float2(v.R[j1].x, v.I[j1].x);
+        const float2 a1 = make_float2(v.R[j].y, v.I[j].y), b1 = make_float2(v.R[j1].y, v.I[j1].y);
+        if (act_y) {
+            const float2 o1 = mv2(m00, a1, m01, b1), p1 = mv2(m10, a1, m11, b1);
+            v.R[j].y = o1.x; v.I[j].y = o1.y; v.R[j1].y = p1.x; v.I[j1].y = p1.y;
+        }
+        if (act_x) {
+            const float2 o0 = mv2(m00, a0, m01, b0), p0 = mv2(m10, a0, m11, b0);
+            v.R[j].x = o0.x; v.I[j].x = o0.y; v.R[j1].x = p0.x; v.I[j1].x = p0.y;
         }
     }
 }
 
-// One gate of a TOP_U2L layer on register bit K, given in rotation form
-// U = e^{i a} diag(1, e^{i p}) [[c, -s], [s, c]] diag(1, e^{i l}) (m = c, s, then a, p,
-// l as 32-bit turns).  The right factor and the pending phase of bit K fold into the
-// butterfly, U diag(1, b) with b = e^{i l} times the pending factor; the left
-// factors become the new pending phases of bit K and of the whole thread (folded
-// into the next gate on that bit, or flushed at the next transpose).  A variant
-// that applied the left factor inside the butterfly when no later gate on the bit
-// follows measured slower: the second code path raised register spills.
-template <int K>
-__device__ __forceinline__ void layer_gate(Regs &v, Pending &pd, const float *m) {
-    const float c = m[0], s = m[1];
-    const uint32_t ta = __float_as_uint(m[2]), tp = __float_as_uint(m[3]);
-    uint32_t tb = __float_as_uint(m[4]);
-    if (pd.mask & (1 << K)) tb += pd.t(K);
-    float2 m01 = make_float2(-s, 0.f), m11 = make_float2(c, 0.f);
-    if (tb != 0) {
-        const float2 b = turns_to_phase(tb);
-        m01 = make_float2(-s * b.x, -s * b.y);
-        m11 = make_float2(c * b.x, c * b.y);
+// General 2x2 gate on register bit 0: the pair is the two halves of one float2.
+__device__ __forceinline__ void u2_bit0(Regs &v, float2 m00, float2 m01, float2 m10, float2 m11, int rmask,
+                                        int rval) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (((j << 1) & rmask) != rval) continue;
+        const float2 a = make_float2(v.R[j].x, v.I[j].x), b = make_float2(v.R[j].y, v.I[j].y);
+        const float2 o0 = make_float2(m00.x * a.x - m00.y * a.y + m01.x * b.x - m01.y * b.y,
+                                      m00.x * a.y + m00.y * a.x + m01.x * b.y + m01.y * b.x);
+        const float2 o1 = make_float2(m10.x * a.x - m10.y * a.y + m11.x * b.x - m11.y * b.y,
+                                      m10.x * a.y + m10.y * a.x + m11.x * b.y + m11.y * b.x);
+        v.R[j] = make_float2(o0.x, o1.x);
+        v.I[j] = make_float2(o0.y, o1.y);
     }
-    rot_butterfly<K>(v, c, s, m01, m11);
-    pd.t(K) = tp;
-    if (tp != 0) pd.mask |= 1 << K;
-    else pd.mask &= ~(1 << K);
-    if (ta != 0) pd.add0(ta);
 }
 
-// amplitudes whose register bits K and L are both 1 are multiplied by f (or negated)
+// amplitudes whose register bits K and L have the values of pat (bit 0: K, bit 1:
+// L) are multiplied by f
 template <int K, int L, int r>
-__device__ __forceinline__ void pair_one(Regs &v, float2 f, bool neg) {
-    if constexpr (((r >> K) & 1) && ((r >> L) & 1)) {
+__device__ __forceinline__ void pair_one(Regs &v, float2 f, int pat) {
+    constexpr int rp = ((r >> K) & 1) | (((r >> L) & 1) << 1);
+    if (pat == rp) {
         float &x = re_of<r>(v);
         float &y = im_of<r>(v);
-        if (neg) {
-            x = -x;
-            y = -y;
-        } else {
-            const float xr = x, xi = y;
-            x = xr * f.x - xi * f.y;
-            y = xr * f.y + xi * f.x;
-        }
+        const float xr = x, xi = y;
+        x = xr * f.x - xi * f.y;
+        y = xr * f.y + xi * f.x;
     }
 }
 template <int K, int L, int... rs>
-__device__ __forceinline__ void pair_all(Regs &v, float2 f, bool neg, std::integer_sequence<int, rs...>) {
-    (pair_one<K, L, rs>(v, f, neg), ...);
+__device__ __forceinline__ void pair_all(Regs &v, float2 f, int pat, std::integer_sequence<int, rs...>) {
+    (pair_one<K, L, rs>(v, f, pat), ...);
 }
 template <int K, int L>
-__device__ __forceinline__ void pair_factor(Regs &v, float2 f, bool neg) {
-    pair_all<K, L>(v, f, neg, std::make_integer_sequence<int, 32>{});
+__device__ __forceinline__ void pair_factor(Regs &v, float2 f, int pat) {
+    pair_all<K, L>(v, f, pat, std::make_integer_sequence<int, 32>{});
+}
+
+template <int K, int L, int r>
+__device__ __forceinline__ void pair_neg_one(Regs &v) {
+    if constexpr (((r >> K) & 1) && ((r >> L) & 1)) {
+        re_of<r>(v) = -re_of<r>(v);
+        im_of<r>(v) = -im_of<r>(v);
+    }
+}
+template <int K, int L, int... rs>
+__device__ __forceinline__ void pair_neg_all(Regs &v, std::integer_sequence<int, rs...>) {
+    (pair_neg_one<K, L, rs>(v), ...);
+}
+// sign flip of the amplitudes whose register bits k and l are both 1 (code k | l << 3)
+__device__ __forceinline__ void pair_neg(Regs &v, int code) {
+    constexpr auto seq = std::make_integer_sequence<int, 32>{};
+    switch (code) {
+        case 0 | (1 << 3): pair_neg_all<0, 1>(v, seq); break;
+        case 0 | (2 << 3): pair_neg_all<0, 2>(v, seq); break;
+        case 0 | (3 << 3): pair_neg_all<0, 3>(v, seq); break;
+        case 0 | (4 << 3): pair_neg_all<0, 4>(v, seq); break;
+        case 1 | (2 << 3): pair_neg_all<1, 2>(v, seq); break;
+        case 1 | (3 << 3): pair_neg_all<1, 3>(v, seq); break;
+        case 1 | (4 << 3): pair_neg_all<1, 4>(v, seq); break;
+        case 2 | (3 << 3): pair_neg_all<2, 3>(v, seq); break;
+        case 2 | (4 << 3): pair_neg_all<2, 4>(v, seq); break;
+        default: pair_neg_all<3, 4>(v, seq); break;
+    }
 }
 
 // fixed-bit masks and the tile base in the offset width (32 bits while n <= 32)
@@ -418,9 +469,21 @@ struct Offsets {
         o23[0] = 0; o23[1] = s2; o23[2] = s3; o23[3] = s2 + s3;
         s4 = s4_;
     }
+    // register bit b of the index is inverted where bit b of f is set
+    __device__ __forceinline__ void init_flipped(Off s0, Off s1, Off s2, Off s3, Off s4_, int f) {
+        const Off a0 = (f & 1) ? s0 : 0, b0 = (f & 1) ? 0 : s0;   // offset of register bit 0 = 0 / 1
+        const Off a1 = (f & 2) ? s1 : 0, b1 = (f & 2) ? 0 : s1;
+        const Off a2 = (f & 4) ? s2 : 0, b2 = (f & 4) ? 0 : s2;
+        const Off a3 = (f & 8) ? s3 : 0, b3 = (f & 8) ? 0 : s3;
+        o01[0] = a0 + a1; o01[1] = b0 + a1; o01[2] = a0 + b1; o01[3] = b0 + b1;
+        o23[0] = a2 + a3; o23[1] = b2 + a3; o23[2] = a2 + b3; o23[3] = b2 + b3;
+        s4 = (f & 16) ? 0 : s4_;
+        s4z = (f & 16) ? s4_ : 0;
+    }
+    Off s4z = 0;   // offset of register bit 4 = 0 (nonzero only when that bit is flipped)
     template <int r>
     __device__ __forceinline__ Off at() const {
-        return o01[r & 3] + o23[(r >> 2) & 3] + ((r & 16) ? s4 : (Off)0);
+        return o01[r & 3] + o23[(r >> 2) & 3] + ((r & 16) ? s4 : s4z);
     }
 };
 
@@ -437,16 +500,97 @@ __device__ __forceinline__ void store_all(float2 *dst, const Offsets<Off> &o, Re
     ((dst[o.template at<rs>()] = make_float2(re_of<rs>(v), im_of<rs>(v))), ...);
 }
 
+// The op kinds a layered circuit rarely needs: controlled / conditioned 2x2
+// gates, conditioned or complex pair factors, direct diagonal factors.
+template <typename Off>
+__device__ __forceinline__ void general_op(Regs &v, DevPending &pd, const TileOp &op, int tbits, Off base,
+                                           unsigned condok) {
+    if (op.kind == TOP_U2) pd.add(op.k, op.hturns);  // uniform part, in every thread
+    if (!op_applies<Off>(op, tbits, base, condok)) return;
+    if (op.kind == TOP_PAIR) {
+        const float2 f = make_float2(op.ph.re, op.ph.im);
+        const int pat = op.rval;   // values of the pair's bits (bit 0: k, bit 1: l)
+        switch (op.k) {
+            case 0 | (1 << 3): pair_factor<0, 1>(v, f, pat); break;
+            case 0 | (2 << 3): pair_factor<0, 2>(v, f, pat); break;
+            case 0 | (3 << 3): pair_factor<0, 3>(v, f, pat); break;
+            case 0 | (4 << 3): pair_factor<0, 4>(v, f, pat); break;
+            case 1 | (2 << 3): pair_factor<1, 2>(v, f, pat); break;
+            case 1 | (3 << 3): pair_factor<1, 3>(v, f, pat); break;
+            case 1 | (4 << 3): pair_factor<1, 4>(v, f, pat); break;
+            case 2 | (3 << 3): pair_factor<2, 3>(v, f, pat); break;
+            case 2 | (4 << 3): pair_factor<2, 4>(v, f, pat); break;
+            default: pair_factor<3, 4>(v, f, pat); break;
+        }
+        return;
+    }
+    if (op.kind == TOP_U2) {
+        float2 m00 = make_float2(op.m[0], op.m[1]), m01 = make_float2(op.m[2], op.m[3]);
+        float2 m10 = make_float2(op.m[4], op.m[5]), m11 = make_float2(op.m[6], op.m[7]);
+        const int k = op.k;
+        const uint32_t tk = pd.get(k);
+        if (tk != 0u) {
+            const float2 ak = phase_of(tk);
+            if (op.rmask == 0) {  // fold diag(1, a_k) into the gate: U * diag(1, a_k)
+                m01 = cmul(m01, ak);
+                m11 = cmul(m11, ak);
+            } else {
+                bit_factor_dispatch(k, v, ak);
+            }
+        }
+        pd.clear(k);
+        if (k == 0) {
+            u2_bit0(v, m00, m01, m10, m11, op.rmask, op.rval);
+        } else {
+            switch (k) {
+                case 1: u2_packed<1>(v, m00, m01, m10, m11, op.rmask, op.rval); break;
+                case 2: u2_packed<2>(v, m00, m01, m10, m11, op.rmask, op.rval); break;
+                case 3: u2_packed<3>(v, m00, m01, m10, m11, op.rmask, op.rval); break;
+                default: u2_packed<4>(v, m00, m01, m10, m11, op.rmask, op.rval); break;
+            }
+        }
+    } else if (op.kind == TOP_PHASE) {  // factor where (register index & rmask) == rval
+        const int rm = op.rmask;
+        const int pc = __popc(rm);
+        if (pc == 0) {
+            pd.add(5, op.ph.turns);
+        } else if (pc == 1) {
+            const int k = __ffs(rm) - 1;
+            if (op.rval) {
+                pd.add(k, op.ph.turns);
+            } else {  // f on bit k = 0:  f * (f^-1 on bit k = 1)
+                pd.add(5, op.ph.turns);
+                pd.add(k, 0u - op.ph.turns);
+            }
+        } else {
+            const int rv = op.rval;
+            const float2 f = make_float2(op.ph.re, op.ph.im);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if (((2 * j) & rm) == rv) {
+                    const float xr = v.R[j].x, xi = v.I[j].x;
+                    v.R[j].x = xr * f.x - xi * f.y;
+                    v.I[j].x = xr * f.y + xi * f.x;
+                }
+                if (((2 * j + 1) & rm) == rv) {
+                    const float xr = v.R[j].y, xi = v.I[j].y;
+                    v.R[j].y = xr * f.x - xi * f.y;
+                    v.I[j].y = xr * f.y + xi * f.x;
+                }
+            }
+        }
+    }
+}
+
 template <typename Off>
 __global__ void __launch_bounds__(kTileThreads, 2)
     k_tile(float2 *__restrict__ psi, const __grid_constant__ TileParams P, const TileEntries *__restrict__ tab,
            const uint8_t *__restrict__ cbits) {
-    // 2 x 2^13 floats (64 KiB) for transposes, then per thread five flush factors, six
-    // pending words and one word per TOP_PHASES op
+    // 2 x 2^13 floats (64 KiB) for transposes, then per thread six pending words
+    // and one word per TOP_PHASES op, then one word per pattern
     extern __shared__ __align__(16) float smf[];
     float *sre = smf, *sim = smf + (1 << kTileQubits);
-    float2 *sfa = reinterpret_cast<float2 *>(smf + (2 << kTileQubits));       // flush factors
-    uint32_t *spd = reinterpret_cast<uint32_t *>(sfa + 5 * kTileThreads);       // pending sums
+    uint32_t *spd = reinterpret_cast<uint32_t *>(smf + (2 << kTileQubits));     // pending sums
     uint32_t *sph = spd + 6 * kTileThreads;                                      // phase-op sums
     uint32_t *spat = sph + P.nphops * kTileThreads;                              // pattern sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -467,10 +611,28 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         condok |= (ok ? 1u : 0u) << c;
     }
 
-    for (uint64_t tile = blockIdx.x; tile < P.n_tiles; tile += gridDim.x) {
+    // one tile per CTA (a grid-stride loop would keep the tile's addressing state
+    // live across iterations and push the kernel into spills)
+    {
+        const uint64_t tile = blockIdx.x;
         uint64_t base64 = 0;
         for (int b = 0; b < P.nfix; ++b) base64 |= ((tile >> b) & 1ull) << P.fixed[b];
         const Off base = (Off)base64;
+
+        // ask L2 for the tile a CTA about one wave later will load (one 256-byte
+        // chunk per thread), so that its HBM reads overlap this CTA's work
+        if (P.pf_dist && tile + P.pf_dist < P.n_tiles) {
+            const uint64_t t2 = tile + P.pf_dist;
+            uint64_t b2 = 0;
+            for (int b = 0; b < P.nfix; ++b) b2 |= ((t2 >> b) & 1ull) << P.fixed[b];
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                if ((lane >> j) & 1) b2 += 1ull << P.S[5 + j];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if ((warp >> j) & 1) b2 += 1ull << P.S[10 + j];
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" ::"l"(psi + b2) : "memory");
+        }
 
         // load in ARR_IO: lanes = local 0..4, registers = local 5..9, warps = local 10..12
         Regs v;
@@ -511,136 +673,110 @@ __global__ void __launch_bounds__(kTileThreads, 2)
             }
         }
 
-        Pending pd;
+        DevPending pd;
         pd.p = spd + threadIdx.x;
-        pd.fa = sfa + threadIdx.x;
         pd.reset();
         int cur = ARR_IO;
+        const uint32_t tidx = (uint32_t)tile;
         for (int i = 0; i < P.nops; ++i) {
             const TileOp &op = P.ops[i];
-            if (op.kind == TOP_XPOSE) {
-                pd.flush(v);
-                transpose(v, sre, sim, cur, op.k, lane, warp);
-                cur = op.k;
-                continue;
-            }
-            if (op.kind == TOP_U2L) {
-                const float *mp = P.mats[op.first];
-                const int bits = op.k;
-                if (bits & 1) { layer_gate<0>(v, pd, mp); mp += 8; }
-                if (bits & 2) { layer_gate<1>(v, pd, mp); mp += 8; }
-                if (bits & 4) { layer_gate<2>(v, pd, mp); mp += 8; }
-                if (bits & 8) { layer_gate<3>(v, pd, mp); mp += 8; }
-                if (bits & 16) layer_gate<4>(v, pd, mp);
-                continue;
-            }
-            if (op.kind == TOP_PHASES) {
-                const uint32_t acc = sph[op.count2 * kTileThreads + threadIdx.x];
-                if (op.k == 5) {
-                    pd.add0(acc);
-                } else {
-                    pd.add(op.k, acc);
+            switch (op.kind) {
+                case TOP_U2L: {
+                    const LayerGate *lg = &P.lg[op.first];
+                    const int bits = op.k;
+                    if (bits & 1) layer_gate<0>(v, pd, *lg++);
+                    if (bits & 2) layer_gate<1>(v, pd, *lg++);
+                    if (bits & 4) layer_gate<2>(v, pd, *lg++);
+                    if (bits & 8) layer_gate<3>(v, pd, *lg++);
+                    if (bits & 16) layer_gate<4>(v, pd, *lg);
+                    break;
                 }
-                continue;
-            }
-            if (!op_applies<Off>(op, tbits, base, condok)) continue;
-            if (op.kind == TOP_PAIR) {
-                const float2 f = make_float2(op.ph.re, op.ph.im);
-                const bool neg = op.ph.turns == 0x80000000u;
-                switch (op.k) {
-                    case 0 | (1 << 3): pair_factor<0, 1>(v, f, neg); break;
-                    case 0 | (2 << 3): pair_factor<0, 2>(v, f, neg); break;
-                    case 0 | (3 << 3): pair_factor<0, 3>(v, f, neg); break;
-                    case 0 | (4 << 3): pair_factor<0, 4>(v, f, neg); break;
-                    case 1 | (2 << 3): pair_factor<1, 2>(v, f, neg); break;
-                    case 1 | (3 << 3): pair_factor<1, 3>(v, f, neg); break;
-                    case 1 | (4 << 3): pair_factor<1, 4>(v, f, neg); break;
-                    case 2 | (3 << 3): pair_factor<2, 3>(v, f, neg); break;
-                    case 2 | (4 << 3): pair_factor<2, 4>(v, f, neg); break;
-                    default: pair_factor<3, 4>(v, f, neg); break;
-                }
-                continue;
-            }
-            if (op.kind == TOP_U2) {
-                float2 m00 = make_float2(op.m[0], op.m[1]), m01 = make_float2(op.m[2], op.m[3]);
-                float2 m10 = make_float2(op.m[4], op.m[5]), m11 = make_float2(op.m[6], op.m[7]);
-                const int k = op.k;
-                if (pd.mask & (1 << k)) {
-                    const uint32_t tk = pd.t(k);
-                    if (tk != 0) {
-                        const float2 ak = turns_to_phase(tk);
-                        if (op.rmask == 0) {  // fold diag(1, a_k) into the gate: U * diag(1, a_k)
-                            m01 = cmul(m01, ak);
-                            m11 = cmul(m11, ak);
+                case TOP_PAIRNEG:
+                    pair_neg(v, op.k);
+                    break;
+                case TOP_PHASEL: {
+                    uint32_t acc = 0;
+                    const int end = op.first + op.count;
+                    for (int e = op.first; e < end; ++e) {
+                        const LinTerm &L = P.lin[e];
+                        const bool ok = ((tbits & L.tmask) == L.tval) && (L.fbit == 0xff || ((tidx >> L.fbit) & 1u));
+                        acc += ok ? L.turns : 0u;
+                    }
+                    if (acc) {
+                        if (op.rval) {  // the term's qubit is stored flipped: on bit k = 0
+                            pd.add(5, acc);
+                            pd.add(op.k, 0u - acc);
                         } else {
-                            bit_factor_dispatch(k, v, ak);
+                            pd.add(op.k, acc);
                         }
                     }
-                    pd.clear(k);
+                    break;
                 }
-                if (k == 0) {
-                    u2_bit0(v, m00, m01, m10, m11, op.rmask);
-                } else {
-                    const Mat M(m00, m01, m10, m11);
-                    switch (k) {
-                        case 1: u2_packed<1>(v, M, op.rmask); break;
-                        case 2: u2_packed<2>(v, M, op.rmask); break;
-                        case 3: u2_packed<3>(v, M, op.rmask); break;
-                        default: u2_packed<4>(v, M, op.rmask); break;
-                    }
-                }
-            } else if (op.kind == TOP_PHASE) {  // factor where (register index & rmask) == rval
-                const int rm = op.rmask;
-                const int pc = __popc(rm);
-                if (pc == 0) {
-                    pd.add0(op.ph.turns);
-                } else if (pc == 1) {
-                    const int k = __ffs(rm) - 1;
+                case TOP_XPOSE:
+                    flush_dev(v, pd);
+                    transpose(v, sre, sim, cur, op.k, lane, warp);
+                    cur = op.k;
+                    break;
+                case TOP_PHASES: {
+                    const uint32_t acc = sph[op.count2 * kTileThreads + threadIdx.x];
                     if (op.rval) {
-                        pd.add(k, op.ph.turns);
-                    } else {  // f on bit k = 0:  f * (f^-1 on bit k = 1)
-                        pd.add0(op.ph.turns);
-                        pd.add(k, 0u - op.ph.turns);
+                        pd.add(5, acc);
+                        pd.add(op.k, 0u - acc);
+                    } else {
+                        pd.add(op.k, acc);
                     }
-                } else {
-                    const int rv = op.rval;
-                    const float2 f = make_float2(op.ph.re, op.ph.im);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if (((2 * j) & rm) == rv) {
-                            const float xr = v.R[j].x, xi = v.I[j].x;
-                            v.R[j].x = xr * f.x - xi * f.y;
-                            v.I[j].x = xr * f.y + xi * f.x;
-                        }
-                        if (((2 * j + 1) & rm) == rv) {
-                            const float xr = v.R[j].y, xi = v.I[j].y;
-                            v.R[j].y = xr * f.x - xi * f.y;
-                            v.I[j].y = xr * f.y + xi * f.x;
-                        }
-                    }
+                    break;
                 }
+                default:
+                    general_op<Off>(v, pd, op, tbits, base, condok);
+                    break;
             }
         }
-        pd.flush(v);
 
-        // store in ARR_IO or ARR_HI (lanes = local 0..4 in both)
+        // final flush: the thread's own pending phases plus the planner's uniform
+        // ones (register bits, and lane / warp bits as a thread constant) and the
+        // pass's real scale.  The store arrangement is ARR_IO or ARR_HI: lanes =
+        // local 0..4 in both; registers local 5..9 / 8..12, warps local 10..12 / 5..7.
         {
-            uint64_t tb = (uint64_t)base + lane_off;
-            Offsets<Off> o;
-            if (cur == ARR_IO) {
+            const int rb = cur == ARR_IO ? 5 : 8, wb = cur == ARR_IO ? 10 : 5;
+            uint32_t t0 = pd.get0() + P.fin_turns[13];
 #pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    if ((warp >> j) & 1) tb += 1ull << P.S[10 + j];
-                o.init((Off)1 << P.S[5], (Off)1 << P.S[6], (Off)1 << P.S[7], (Off)1 << P.S[8], (Off)1 << P.S[9]);
-            } else {
+            for (int j = 0; j < 5; ++j)
+                if ((lane >> j) & 1) t0 += P.fin_turns[j];
 #pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    if ((warp >> j) & 1) tb += 1ull << P.S[5 + j];
-                o.init((Off)1 << P.S[8], (Off)1 << P.S[9], (Off)1 << P.S[10], (Off)1 << P.S[11], (Off)1 << P.S[12]);
+            for (int j = 0; j < 3; ++j)
+                if ((warp >> j) & 1) t0 += P.fin_turns[wb + j];
+            float2 a[5];
+            bool any = t0 != 0u || P.fin_scale != 1.f;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const uint32_t tk = pd.get(k) + P.fin_turns[rb + k];
+                any = any || tk != 0u;
+                a[k] = phase_of(tk);
             }
+            if (any) {
+                const float2 c0 = phase_of(t0);
+                apply_diagonal(v, make_float2(c0.x * P.fin_scale, c0.y * P.fin_scale), a);
+            }
+        }
+
+        // store in ARR_IO or ARR_HI (lanes = local 0..4 in both); a local qubit the
+        // planner left flipped has its index bit inverted here
+        {
+            const int fl = P.fin_flip;
+            uint64_t tb = (uint64_t)base;
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                if (((lane ^ fl) >> j) & 1) tb += 1ull << P.S[j];
+            const int rb = cur == ARR_IO ? 5 : 8, wb = cur == ARR_IO ? 10 : 5;
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (((warp ^ (fl >> wb)) >> j) & 1) tb += 1ull << P.S[wb + j];
+            Offsets<Off> o;
+            o.init_flipped((Off)1 << P.S[rb], (Off)1 << P.S[rb + 1], (Off)1 << P.S[rb + 2], (Off)1 << P.S[rb + 3],
+                           (Off)1 << P.S[rb + 4], (fl >> rb) & 31);
             store_all<Off>(psi + tb, o, v, std::make_integer_sequence<int, 32>{});
         }
-        __syncthreads();  // shared memory is reused by the next tile's transposes
     }
 }
 
@@ -652,10 +788,11 @@ __global__ void k_tile_entries(const __grid_constant__ TileEntries E, int ne, in
 template <typename Off>
 cudaError_t launch_tile_t(void *psi, const TileParams &p, const TileEntries *entries, const uint8_t *cbits,
                           cudaStream_t s) {
-    // transposes (2^13 complex64), flush factors (5 float2), pending (6 words), phase sums
-    constexpr int smem_max =
-        ((int)(2 * sizeof(float)) << kTileQubits) + (16 + kTileMaxPhOps) * kTileThreads * 4 + kTileMaxPats * 4;
-    const int smem = ((int)(2 * sizeof(float)) << kTileQubits) + (16 + p.nphops) * kTileThreads * 4 +
+    // transposes (2^13 complex64), pending sums (6 words per thread), phase-op sums
+    // (one word per thread each), pattern sums
+    constexpr int smem_max = ((int)(2 * sizeof(float)) << kTileQubits) + (6 + kTileMaxPhOps) * kTileThreads * 4 +
+                             kTileMaxPats * 4;
+    const int smem = ((int)(2 * sizeof(float)) << kTileQubits) + (6 + p.nphops) * kTileThreads * 4 +
                      (p.nphops ? p.npats * 4 : 0);
     // the shared-memory attribute is set once per device
     static bool attr_set[64] = {false};
@@ -668,9 +805,8 @@ cudaError_t launch_tile_t(void *psi, const TileParams &p, const TileEntries *ent
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
-    uint64_t grid = p.n_tiles;
-    if (grid > (1ull << 30)) grid = 1ull << 30;
-    k_tile<Off><<<(unsigned)grid, kTileThreads, smem, s>>>((float2 *)psi, p, entries, cbits);
+    if (p.n_tiles == 0 || p.n_tiles > (1ull << 31) - 1) return cudaErrorInvalidValue;
+    k_tile<Off><<<(unsigned)p.n_tiles, kTileThreads, smem, s>>>((float2 *)psi, p, entries, cbits);
     return cudaGetLastError();
 }
 

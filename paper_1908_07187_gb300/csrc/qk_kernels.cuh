@@ -254,23 +254,46 @@ constexpr int kTileContig = 5;
 constexpr int kTileThreads = 256;
 constexpr int kTileMaxOps = 192;
 constexpr int kTileMaxEntries = 512;
-constexpr int kTileMaxPats = 320;
+constexpr int kTileMaxPats = 64;
+constexpr int kTileMaxLin = 512;
 constexpr int kTileMaxMats = 160;
 constexpr int kTileMaxConds = 4;
 constexpr int kTileMaxPhOps = 24;   // TOP_PHASES ops per pass (their sums live in shared memory)
 enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
-// TOP_PHASES: a group of diagonal terms that all add to one pending phase sum
-// (register bit k, or the constant when k == 5), as patterns [first, first +
-// count): each pattern is the terms sharing one thread-bit condition; its
-// fixed-bit-conditioned terms are entries in global memory, summed by the lanes
-// of a warp in parallel (the condition is uniform over a tile).  The sums do not
-// depend on the amplitudes, so every TOP_PHASES op of a pass is summed when a
-// tile starts and kept in shared memory (slot count2) until the op runs.
+// TOP_PHASES: a group of thread- or tile-dependent diagonal terms that all add to
+// one pending phase sum (register bit k, or the thread constant when k == 5), as
+// patterns [first, first + count): each pattern is the terms sharing one
+// thread-bit condition; its fixed-bit-conditioned terms are entries in global
+// memory, summed by one thread per pattern (the condition is uniform over a
+// tile).  The sums do not depend on the amplitudes, so every TOP_PHASES op of a
+// pass is summed when a tile starts and kept in shared memory (slot count2) until
+// the op runs.  Diagonal terms that are the same for every amplitude pair of a
+// qubit (no thread or fixed-bit condition) never reach the device: the planner
+// folds them into the next layer gate's coefficients or into the final flush.
 // TOP_U2L: a layer of uncontrolled 2x2 gates on distinct register bits (k is
-// the bit mask); their matrices are mats[first...] in bit order.
+// the bit mask), in pivot form; their coefficients are lg[first...] in bit order.
 // TOP_PAIR: factor on the amplitudes whose register bits k and l are both 1
 // (code k | l << 3), under the op's thread / fixed-bit conditions.
-enum TileOpKind : uint8_t { TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_PHASES = 3, TOP_U2L = 4, TOP_PAIR = 5 };
+// TOP_PHASEL: the common form of such a group, a sum of linear terms lin[first,
+// first + count) evaluated in place (see LinTerm).  For TOP_PHASES and TOP_PHASEL,
+// rval = 1 says that bit k's qubit is stored flipped, so the sum lands on k = 0.
+// TOP_PAIR: rval holds the values of the pair's two bits that the factor needs.
+// TOP_PAIRNEG: an unconditional sign flip of the amplitudes whose register bits k
+// and l are both 1 (code k | l << 3): a CZ between two register bits.
+enum TileOpKind : uint8_t {
+    TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_PHASES = 3, TOP_U2L = 4, TOP_PAIR = 5, TOP_PHASEL = 6,
+    TOP_PAIRNEG = 7
+};
+
+// A diagonal term of a TOP_PHASEL group: adds turns where the thread bits match
+// (tbits & tmask) == tval and, unless fbit == 0xff, bit fbit of the tile index
+// (the fixed qubit P.fixed[fbit]) is 1.  Terms on a fixed qubit being 0 are
+// written as the unconditional term minus the conditional one.
+struct LinTerm {
+    uint16_t tmask, tval;
+    uint8_t fbit, pad[3];
+    uint32_t turns;
+};
 
 // A diagonal term conditioned on fixed (non-tile) bits: adds turns when
 // (tile base & gmask) == gval.
@@ -292,6 +315,21 @@ struct TileEntries {
     PhasePattern p[kTileMaxPats];
 };
 
+// One gate of a TOP_U2L layer in pivot form.  The planner may keep a local
+// qubit's two values stored swapped ("flipped"); it picks the stored order of the
+// gate's output so that, with M the gate in stored order and the pending factor F
+// of the bit folded in, M diag(1, F) has its larger entries on the diagonal
+// (|M00| = |M11| >= |M10| = |M01|).  It is applied to a pair (y0, y1) as
+//   z0 = y0 + a0 y1,  z1 = y1 + a1 y0,   a0 = M01 F / M00,  a1 = M10 / (M11 F),
+// and the true outputs are (M00 z0, M11 F z1): |a0|, |a1| <= 1 and 8 FMAs per pair.
+// |M00| >= 1/sqrt 2 is one real scale for the whole pass and the phases of M00
+// and M11 F / M00 become pending phases, both tracked by the planner.  The
+// device uses a0 = A0 e and a1 = A1 conj(e), with e the thread-dependent part of
+// F; c[] holds A0, A1 as FFMA2 operand pairs (re, re), (im, im), (-im, -im).
+struct LayerGate {
+    float2 c[6];           // A0r, A0i, -A0i, A1r, A1i, -A1i, each splatted
+};
+
 struct TileOp {
     uint8_t kind;          // TileOpKind
     uint8_t k;             // U2: target register bit; XPOSE: new arrangement
@@ -299,8 +337,11 @@ struct TileOp {
     uint16_t tmask, tval;  // condition on thread bits: bits 0..4 lane, 5..7 warp
     uint16_t cond;         // index into TileParams::conds, 0xffff = unconditional
     uint16_t count;        // TOP_PHASES: patterns [first, first + count); TOP_U2L: gates
-    uint16_t first;        //   from mats[first]
+    uint16_t first;        //   from lg[first]
     uint16_t count2;
+    uint32_t hturns;       // TOP_U2: uniform pending turns of the target's qubit, added
+                           // to the thread's pending sum before the op
+    uint32_t pad;
     uint64_t gmask, gval;  // condition on the tile's fixed (non-tile) physical bits
     union {
         float m[8];        // U2: m00, m01, m10, m11 as (re, im)
@@ -325,9 +366,16 @@ struct TileParams {
     int npats;
     int nphops;                             // TOP_PHASES ops; op.count2 is the op's slot
     uint16_t phop[kTileMaxPhOps][2];        // slot -> (first pattern, pattern count)
+    // final flush: the uniform pending phase of each local qubit's |1> (turns), the
+    // uniform constant phase (fin_turns[13]) and the pass's real scale
+    uint32_t fin_turns[14];
+    float fin_scale;
+    int fin_flip;          // local qubits stored flipped at the end (bit b: local qubit b)
+    uint32_t pf_dist;      // L2 prefetch of the tile this many CTAs ahead (0: none)
     TileOp ops[kTileMaxOps];
     PhasePattern pats[kTileMaxPats];
-    float mats[kTileMaxMats][8];
+    LayerGate lg[kTileMaxMats];
+    LinTerm lin[kTileMaxLin];
 };
 static_assert(sizeof(TileParams) <= 32764, "tile program must fit in the kernel parameter space");
 

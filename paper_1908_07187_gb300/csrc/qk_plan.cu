@@ -11,6 +11,12 @@
 // Qubits join S greedily as 2x2 targets are met.  Inside the pass the taken
 // gates are list-scheduled over the three register arrangements of the tile
 // kernel, inserting a transpose when no ready gate fits the current one.
+//
+// A last walk over the program (fold_program) turns each layer gate into pivot
+// form (LayerGate in qk_kernels.cuh) and keeps, in double precision, every
+// pending phase that is the same for all threads -- per local qubit, plus a
+// constant -- and the pass's real scale: those fold into later gates'
+// coefficients and the final flush, so the device never sees them.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -122,38 +128,73 @@ void encode_cond(uint64_t mask, uint64_t val, int arr, const int *local_of, Tile
     }
 }
 
-// A 2x2 unitary as e^{i a} diag(1, e^{i p}) [[c, -s], [s, c]] diag(1, e^{i l}) with c, s
-// real (c may be negative, s >= 0); the layer kernel stores c, s and a, p, l in 32-bit
-// fixed-point turns.  a is the phase of u00 folded into (-pi/2, pi/2] so that c =
-// e^{-i a} u00 is real; then u10 = e^{i a} s e^{i p}, u01 = -e^{i a} s e^{i l}, and
-// for s = 0 the phase of u11 / c fixes p (l = 0).
 uint32_t angle_turns(double x) {
     double frac = x / (2.0 * M_PI);
     frac -= std::floor(frac);
     return (uint32_t)(uint64_t)std::llround(frac * 4294967296.0);
 }
-void rotation_form(const float *m, float *out) {
-    const std::complex<double> u00(m[0], m[1]), u01(m[2], m[3]), u10(m[4], m[5]), u11(m[6], m[7]);
-    double a = std::abs(u00) > 0 ? std::arg(u00) : 0.0;
-    if (a > M_PI / 2) a -= M_PI;
-    if (a <= -M_PI / 2) a += M_PI;
-    const std::complex<double> ea = std::polar(1.0, -a);
-    const double c = (u00 * ea).real();
-    const double s = std::abs(u10);
-    double p = 0.0, l = 0.0;
-    if (s > 0) {
-        p = std::arg(u10 * ea);
-        l = std::arg(-u01 * ea);
-    } else {
-        p = std::arg(u11 * ea / c);
+double turns_angle(uint32_t t) { return 2.0 * M_PI * (double)t / 4294967296.0; }
+
+// local qubit of register bit k in an arrangement
+int local_of_reg(int arr, int k) { return arr == ARR_IO ? 5 + k : arr == ARR_LO ? k : 8 + k; }
+
+// Planner-only op kind: a diagonal term that is the same for every thread and
+// tile (no thread or fixed-bit condition) on register bit k (k == 5: constant),
+// ph.turns; fold_program absorbs it and it never reaches the device.
+constexpr uint8_t TOP_HOSTPH = 0x40;
+
+using cdm = std::complex<double>;
+struct Mat2 {
+    cdm m[4];
+};
+
+// The program's pending state that is the same for every thread, in double
+// precision: u[q] the phase of local qubit q's stored |1> relative to its stored
+// |0>, u0 a constant phase, lam the real scale that the pivot form leaves over,
+// flip[q] whether q's values are stored swapped.
+struct UniformPending {
+    double u[kTileQubits] = {};
+    double u0 = 0.0;
+    double lam = 1.0;
+    int flip[kTileQubits] = {};   // local qubit stored with its two values swapped
+};
+
+// Pivot form of a layer gate on local qubit q (LayerGate in qk_kernels.cuh).  The
+// gate in stored order is W = U X^f (f: q stored flipped); the output is stored
+// flipped (f') when that puts the larger entries of M = X^f' W on the diagonal.
+// F = e^{i u[q]} is the pending phase of q's stored |1>.
+void pivot_gate(const Mat2 &g, UniformPending &st, int q, LayerGate &out) {
+    cdm W[4] = {g.m[0], g.m[1], g.m[2], g.m[3]};
+    if (st.flip[q]) {  // U X: swap the columns
+        std::swap(W[0], W[1]);
+        std::swap(W[2], W[3]);
     }
-    const uint32_t t[3] = {angle_turns(a), angle_turns(p), angle_turns(l)};
-    out[0] = (float)c;
-    out[1] = (float)s;
-    std::memcpy(&out[2], t, sizeof t);
-    out[5] = out[6] = out[7] = 0.f;
+    const bool fout = std::abs(W[0]) < std::abs(W[2]);
+    if (fout) {        // X W: swap the rows
+        std::swap(W[0], W[2]);
+        std::swap(W[1], W[3]);
+    }
+    const cdm m00 = W[0], m01 = W[1], m10 = W[2], m11 = W[3];
+    const cdm F = std::polar(1.0, st.u[q]);
+    const cdm A0 = m01 * F / m00, A1 = m10 / (m11 * F);
+    st.u0 += std::arg(m00);
+    st.u[q] += std::arg(m11) - std::arg(m00);
+    st.lam *= std::abs(m00);
+    st.flip[q] = fout ? 1 : 0;
+    const float a0r = (float)A0.real(), a0i = (float)A0.imag(), a1r = (float)A1.real(), a1i = (float)A1.imag();
+    out.c[0] = make_float2(a0r, a0r);
+    out.c[1] = make_float2(a0i, a0i);
+    out.c[2] = make_float2(-a0i, -a0i);
+    out.c[3] = make_float2(a1r, a1r);
+    out.c[4] = make_float2(a1i, a1i);
+    out.c[5] = make_float2(-a1i, -a1i);
 }
 
+// local qubits of the thread bits (0..4 lanes, 5..7 warps) in an arrangement
+int local_of_tbit(int arr, int t) {
+    if (t < 5) return arr == ARR_LO ? 5 + t : t;
+    return arr == ARR_HI ? 5 + (t - 5) : 10 + (t - 5);
+}
 }  // namespace
 
 qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> &ops) {
@@ -269,6 +310,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 int pos;
                 slot_of(arr, local_of[op.q], &pos);
                 t.k = (uint8_t)pos;
+                t.first = (uint16_t)j;   // the FP64 matrix: taken[j]
                 encode_cond(op.cmask, op.cmask, arr, local_of, t);
                 for (int e = 0; e < 4; ++e) {
                     t.m[2 * e] = (float)op.m[e].real();
@@ -327,7 +369,10 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
         // group runs of consecutive diagonal terms by the pending sum they feed
         {
             static thread_local TileOp out[2 * kTileMaxOps + 8];
-            int nout = 0, nent = 0, npat = 0, nph = 0;
+            int nout = 0, nent = 0, npat = 0, nph = 0, nlin = 0;
+            int fixed_index[64];   // physical qubit -> bit of the tile index
+            for (int b = 0; b < 64; ++b) fixed_index[b] = -1;
+            for (int b = 0; b < P.nfix; ++b) fixed_index[(int)P.fixed[b]] = b;
             bool overflow = false;
             for (int i = 0; i < nops && !overflow;) {
                 if (nout >= 2 * kTileMaxOps) {
@@ -423,13 +468,18 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                     }
                     TileOp &t = out[nout++];
                     std::memset(&t, 0, sizeof t);
-                    t.kind = TOP_PAIR;
+                    t.cond = 0xffff;
                     t.k = (uint8_t)pk.code;
+                    if (pk.tmask == 0 && pk.gmask == 0 && pk.turns == 0x80000000u) {
+                        t.kind = TOP_PAIRNEG;   // a CZ between two register bits
+                        continue;
+                    }
+                    t.kind = TOP_PAIR;
+                    t.rval = 3;   // both bits 1
                     t.tmask = pk.tmask;
                     t.tval = pk.tval;
                     t.gmask = pk.gmask;
                     t.gval = pk.gval;
-                    t.cond = 0xffff;
                     const double ang = 2.0 * M_PI * (double)pk.turns / 4294967296.0;
                     t.ph.re = (float)std::cos(ang);
                     t.ph.im = (float)std::sin(ang);
@@ -437,44 +487,101 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 }
                 for (int g = 0; g < 6 && !overflow; ++g) {
                     if (grp[g].empty()) continue;
-                    // patterns: the group's terms by thread-bit condition; within one,
-                    // terms with equal fixed-bit conditions merge, and those with none
-                    // become the pattern's constant
-                    std::sort(grp[g].begin(), grp[g].end(), [](const Term &a, const Term &b) {
+                    // split the group's terms: the same for every thread (kept by the
+                    // planner), linear (thread-bit condition and at most one fixed
+                    // qubit that must be 1: TOP_PHASEL), general (TOP_PHASES)
+                    uint32_t host_turns = 0;
+                    std::vector<LinTerm> lins;
+                    std::vector<Term> general;
+                    auto add_lin = [&](uint16_t tm, uint16_t tv, uint8_t fb, uint32_t tu) {
+                        for (auto &l : lins)
+                            if (l.tmask == tm && l.tval == tv && l.fbit == fb) {
+                                l.turns += tu;
+                                return;
+                            }
+                        LinTerm l{};
+                        l.tmask = tm;
+                        l.tval = tv;
+                        l.fbit = fb;
+                        l.turns = tu;
+                        lins.push_back(l);
+                    };
+                    for (const Term &t : grp[g]) {
+                        if (t.gmask == 0) {
+                            if (t.tmask == 0) host_turns += t.turns;
+                            else add_lin(t.tmask, t.tval, 0xff, t.turns);
+                        } else if (__builtin_popcountll(t.gmask) == 1) {
+                            const uint8_t fb = (uint8_t)fixed_index[__builtin_ctzll(t.gmask)];
+                            if (t.gval) {
+                                add_lin(t.tmask, t.tval, fb, t.turns);
+                            } else {  // on the fixed qubit being 0: unconditional minus on 1
+                                if (t.tmask == 0) host_turns += t.turns;
+                                else add_lin(t.tmask, t.tval, 0xff, t.turns);
+                                add_lin(t.tmask, t.tval, fb, 0u - t.turns);
+                            }
+                        } else {
+                            general.push_back(t);
+                        }
+                    }
+                    if (host_turns != 0) {
+                        if (nout >= 2 * kTileMaxOps) { overflow = true; break; }
+                        TileOp &t = out[nout++];
+                        std::memset(&t, 0, sizeof t);
+                        t.kind = TOP_HOSTPH;
+                        t.k = (uint8_t)g;
+                        t.cond = 0xffff;
+                        t.ph.turns = host_turns;
+                    }
+                    int nl = 0;
+                    for (const auto &l : lins) nl += l.turns != 0;
+                    if (nl) {
+                        if (nout >= 2 * kTileMaxOps || nlin + nl > kTileMaxLin) { overflow = true; break; }
+                        TileOp &t = out[nout++];
+                        std::memset(&t, 0, sizeof t);
+                        t.kind = TOP_PHASEL;
+                        t.k = (uint8_t)g;
+                        t.cond = 0xffff;
+                        t.first = (uint16_t)nlin;
+                        for (const auto &l : lins)
+                            if (l.turns != 0) P.lin[nlin++] = l;
+                        t.count = (uint16_t)(nlin - t.first);
+                    }
+                    if (general.empty()) continue;
+                    // patterns: the general terms by thread-bit condition; within one,
+                    // terms with equal fixed-bit conditions merge
+                    std::sort(general.begin(), general.end(), [](const Term &a, const Term &b) {
                         if (a.tmask != b.tmask) return a.tmask < b.tmask;
                         if (a.tval != b.tval) return a.tval < b.tval;
                         if (a.gmask != b.gmask) return a.gmask < b.gmask;
                         return a.gval < b.gval;
                     });
                     const int pat0 = npat;
-                    for (size_t a = 0; a < grp[g].size() && !overflow;) {
+                    for (size_t a = 0; a < general.size() && !overflow;) {
                         size_t b = a;
-                        while (b < grp[g].size() && grp[g][b].tmask == grp[g][a].tmask &&
-                               grp[g][b].tval == grp[g][a].tval)
+                        while (b < general.size() && general[b].tmask == general[a].tmask &&
+                               general[b].tval == general[a].tval)
                             ++b;
                         PhasePattern pt{};
-                        pt.tmask = grp[g][a].tmask;
-                        pt.tval = grp[g][a].tval;
+                        pt.tmask = general[a].tmask;
+                        pt.tval = general[a].tval;
                         pt.first = (uint16_t)nent;
                         for (size_t x = a; x < b;) {
                             size_t y = x;
                             uint32_t tu = 0;
-                            while (y < b && grp[g][y].gmask == grp[g][x].gmask && grp[g][y].gval == grp[g][x].gval)
-                                tu += grp[g][y++].turns;
-                            if (grp[g][x].gmask == 0) {
-                                pt.turns += tu;
-                            } else if (tu != 0) {
+                            while (y < b && general[y].gmask == general[x].gmask && general[y].gval == general[x].gval)
+                                tu += general[y++].turns;
+                            if (tu != 0) {
                                 if (nent >= kTileMaxEntries) { overflow = true; break; }
                                 PhaseEntry &e = E.e[nent++];
-                                e.gmask = grp[g][x].gmask;
-                                e.gval = grp[g][x].gval;
+                                e.gmask = general[x].gmask;
+                                e.gval = general[x].gval;
                                 e.turns = tu;
                                 e.pad = 0;
                             }
                             x = y;
                         }
                         pt.count = (uint16_t)(nent - pt.first);
-                        if (!overflow && (pt.count || pt.turns)) {
+                        if (!overflow && pt.count) {
                             if (npat >= kTileMaxPats) { overflow = true; break; }
                             E.p[npat] = pt;
                             P.pats[npat++] = pt;
@@ -507,6 +614,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             // merge runs of consecutive uncontrolled 2x2 gates on distinct
             // register bits into layer ops (they commute with each other)
             int nfin = 0, nmat = 0;
+            static thread_local uint16_t lg_mat[kTileMaxMats];   // layer gate -> taken[] index
             for (int i = 0; i < nout && !overflow;) {
                 const TileOp &o = out[i];
                 const bool plain_u2 = o.kind == TOP_U2 && o.rmask == 0 && o.tmask == 0 && o.gmask == 0 &&
@@ -533,10 +641,11 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 t.cond = 0xffff;
                 t.first = (uint16_t)nmat;
                 t.count = (uint16_t)(j - i);
-                // rotation forms (c, s, phase turns a, p, l) in register-bit order
+                // the gates' FP64 matrices in register-bit order; fold_program turns
+                // them into pivot coefficients
                 for (int b = 0; b < 5; ++b)
                     for (int q = i; q < j; ++q)
-                        if (out[q].k == b) rotation_form(out[q].m, P.mats[nmat++]);
+                        if (out[q].k == b) lg_mat[nmat++] = out[q].first;
                 i = j;
             }
             if (overflow) {
@@ -544,6 +653,110 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 max_u2 = std::max(1, max_u2 / 2);
                 max_ph = std::max(1, max_ph / 2);
                 continue;
+            }
+            // fold_program: walk the program in order, keeping the pending phases
+            // that are the same for every thread (and the scale and the stored bit
+            // order of each local qubit) in FP64; layer gates get their pivot
+            // coefficients, every other op's conditions are rewritten to the stored
+            // order, general gates take their target's uniform phase along to the
+            // device, and what is left goes to the final flush
+            {
+                UniformPending st;
+                int arr = ARR_IO, w = 0;
+                const double pi = M_PI;
+                for (int i = 0; i < nfin; ++i) {
+                    TileOp o = P.ops[i];
+                    // flipped register and thread bits in the current arrangement
+                    int rflip = 0, tflip = 0;
+                    for (int k = 0; k < 5; ++k) rflip |= st.flip[local_of_reg(arr, k)] << k;
+                    for (int t = 0; t < 8; ++t) tflip |= st.flip[local_of_tbit(arr, t)] << t;
+                    auto qk_of = [&](int k) { return local_of_reg(arr, k); };
+                    switch (o.kind) {
+                        case TOP_HOSTPH: {
+                            const double ang = turns_angle(o.ph.turns);
+                            if (o.k == 5) {
+                                st.u0 += ang;
+                            } else if (st.flip[qk_of(o.k)]) {  // on the stored |0>
+                                st.u0 += ang;
+                                st.u[qk_of(o.k)] -= ang;
+                            } else {
+                                st.u[qk_of(o.k)] += ang;
+                            }
+                            continue;   // never reaches the device
+                        }
+                        case TOP_XPOSE:
+                            arr = o.k;
+                            break;
+                        case TOP_U2L: {
+                            int idx = o.first;
+                            for (int b = 0; b < 5; ++b) {
+                                if (!((o.k >> b) & 1)) continue;
+                                const FusedOp &fo = *taken[lg_mat[idx]].op;
+                                const Mat2 g{{fo.m[0], fo.m[1], fo.m[2], fo.m[3]}};
+                                pivot_gate(g, st, qk_of(b), P.lg[idx]);
+                                ++idx;
+                            }
+                            break;
+                        }
+                        case TOP_PAIRNEG: {
+                            // (-1)^((a^fa)(b^fb)) = (-1)^(ab) (-1)^(fb a) (-1)^(fa b) (-1)^(fa fb)
+                            const int ka = o.k & 7, kb = o.k >> 3;
+                            const int fa = (rflip >> ka) & 1, fb = (rflip >> kb) & 1;
+                            if (fb) st.u[qk_of(ka)] += pi;
+                            if (fa) st.u[qk_of(kb)] += pi;
+                            if (fa && fb) st.u0 += pi;
+                            break;
+                        }
+                        case TOP_PAIR: {
+                            const int ka = o.k & 7, kb = o.k >> 3;
+                            o.rval = (uint8_t)(3 ^ (((rflip >> ka) & 1) | (((rflip >> kb) & 1) << 1)));
+                            o.tval ^= (uint16_t)(o.tmask & tflip);
+                            break;
+                        }
+                        case TOP_PHASEL:
+                            for (int e = o.first; e < o.first + o.count; ++e)
+                                P.lin[e].tval ^= (uint16_t)(P.lin[e].tmask & tflip);
+                            o.rval = (uint8_t)(o.k < 5 ? (rflip >> o.k) & 1 : 0);
+                            break;
+                        case TOP_PHASES:
+                            for (int q = o.first; q < o.first + o.count; ++q) {
+                                P.pats[q].tval ^= (uint16_t)(P.pats[q].tmask & tflip);
+                                E.p[q].tval = P.pats[q].tval;
+                            }
+                            o.rval = (uint8_t)(o.k < 5 ? (rflip >> o.k) & 1 : 0);
+                            break;
+                        case TOP_PHASE:
+                            o.rval ^= (uint8_t)(o.rmask & rflip);
+                            o.tval ^= (uint16_t)(o.tmask & tflip);
+                            break;
+                        case TOP_U2: {
+                            const int q = qk_of(o.k);
+                            o.rval ^= (uint8_t)(o.rmask & rflip);
+                            o.tval ^= (uint16_t)(o.tmask & tflip);
+                            if (st.flip[q]) {  // X U X in stored order
+                                float t[8];
+                                std::memcpy(t, o.m, sizeof t);
+                                const int perm[4] = {3, 2, 1, 0};
+                                for (int e = 0; e < 4; ++e) {
+                                    o.m[2 * e] = t[2 * perm[e]];
+                                    o.m[2 * e + 1] = t[2 * perm[e] + 1];
+                                }
+                            }
+                            o.hturns = angle_turns(st.u[q]);
+                            st.u[q] = 0.0;
+                            break;
+                        }
+                        default:
+                            break;
+                    }
+                    P.ops[w++] = o;
+                }
+                nfin = w;
+                for (int q = 0; q < kTileQubits; ++q) P.fin_turns[q] = angle_turns(st.u[q]);
+                P.fin_turns[13] = angle_turns(st.u0);
+                P.fin_scale = (float)st.lam;
+                P.fin_flip = 0;
+                for (int q = 0; q < kTileQubits; ++q) P.fin_flip |= st.flip[q] << q;
             }
             nops = nfin;
             P.nentries = nent;
@@ -553,7 +766,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
         P.nops = nops;
         P.store_arr = cur;
         if (planner->log) {
-            int cnt_k[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            int cnt_k[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // by TileOpKind
             for (int i = 0; i < nops; ++i) cnt_k[P.ops[i].kind]++;
             std::fprintf(stderr,
                          "[qk plan] pass S=%#llx gates=%d (u2 %d, phase %d) ops=%d u2=%d layers=%d phase_direct=%d "
@@ -575,6 +788,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             ctx_launch_end(tok);
             if (e != cudaSuccess) return ctx_fail(c, QK_ECUDA, cudaGetErrorString(e));
         }
+        P.pf_dist = (uint32_t)(2 * ctx_sms(c));   // one wave of resident CTAs ahead
         ctx_launch_begin(c, 0, 2.0 * 8.0 * (double)(1ull << n), &tok);
         cudaError_t e = launch_tile(ctx_state(c), P, ctx_tile_entries(c), ctx_cbits(c), ctx_stream(c));
         ctx_launch_end(tok);

@@ -500,6 +500,16 @@ __device__ __forceinline__ void store_all(float2 *dst, const Offsets<Off> &o, Re
     ((dst[o.template at<rs>()] = make_float2(re_of<rs>(v), im_of<rs>(v))), ...);
 }
 
+// Physical index of a tile's base (its local qubits 0): the tile index's bits
+// deposited on the fixed qubits, one run of consecutive qubits at a time.
+__device__ __forceinline__ uint64_t tile_base(const TileParams &P, uint64_t tile) {
+    uint64_t b = 0;
+#pragma unroll
+    for (int r = 0; r < kTileMaxRuns; ++r)
+        if (r < P.nruns) b |= ((tile >> P.run_tlo[r]) & ((1ull << P.run_len[r]) - 1)) << P.run_plo[r];
+    return b;
+}
+
 // The op kinds a layered circuit rarely needs: controlled / conditioned 2x2
 // gates, conditioned or complex pair factors, direct diagonal factors.
 template <typename Off>
@@ -601,38 +611,11 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     for (int j = 0; j < 5; ++j)
         if ((lane >> j) & 1) lane_off += 1ull << P.S[j];
 
-    fill_turn_table();
-    __syncthreads();
-
-    unsigned condok = 0;
-    for (int c = 0; c < P.n_conds; ++c) {
-        bool ok = true;
-        for (int k = 0; k < P.conds[c].n; ++k) ok = ok && cbits[P.conds[c].idx[k]] != 0;
-        condok |= (ok ? 1u : 0u) << c;
-    }
-
     // one tile per CTA (a grid-stride loop would keep the tile's addressing state
     // live across iterations and push the kernel into spills)
     {
         const uint64_t tile = blockIdx.x;
-        uint64_t base64 = 0;
-        for (int b = 0; b < P.nfix; ++b) base64 |= ((tile >> b) & 1ull) << P.fixed[b];
-        const Off base = (Off)base64;
-
-        // ask L2 for the tile a CTA about one wave later will load (one 256-byte
-        // chunk per thread), so that its HBM reads overlap this CTA's work
-        if (P.pf_dist && tile + P.pf_dist < P.n_tiles) {
-            const uint64_t t2 = tile + P.pf_dist;
-            uint64_t b2 = 0;
-            for (int b = 0; b < P.nfix; ++b) b2 |= ((t2 >> b) & 1ull) << P.fixed[b];
-#pragma unroll
-            for (int j = 0; j < 5; ++j)
-                if ((lane >> j) & 1) b2 += 1ull << P.S[5 + j];
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                if ((warp >> j) & 1) b2 += 1ull << P.S[10 + j];
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" ::"l"(psi + b2) : "memory");
-        }
+        const Off base = (Off)tile_base(P, tile);
 
         // load in ARR_IO: lanes = local 0..4, registers = local 5..9, warps = local 10..12
         Regs v;
@@ -645,6 +628,29 @@ __global__ void __launch_bounds__(kTileThreads, 2)
             o.init((Off)1 << P.S[5], (Off)1 << P.S[6], (Off)1 << P.S[7], (Off)1 << P.S[8], (Off)1 << P.S[9]);
             load_all<Off>(psi + tb, o, v, std::make_integer_sequence<int, 32>{});
         }
+
+        // ask L2 for the tile a CTA about one wave later will load (one 256-byte
+        // chunk per thread), so that its HBM reads overlap this CTA's work
+        if (P.pf_dist && tile + P.pf_dist < P.n_tiles) {
+            uint64_t b2 = tile_base(P, tile + P.pf_dist);
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                if ((lane >> j) & 1) b2 += 1ull << P.S[5 + j];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if ((warp >> j) & 1) b2 += 1ull << P.S[10 + j];
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" ::"l"(psi + b2) : "memory");
+        }
+
+        // while the loads are in flight: the phase table, the classical conditions
+        fill_turn_table();
+        unsigned condok = 0;
+        for (int c = 0; c < P.n_conds; ++c) {
+            bool ok = true;
+            for (int k = 0; k < P.conds[c].n; ++k) ok = ok && cbits[P.conds[c].idx[k]] != 0;
+            condok |= (ok ? 1u : 0u) << c;
+        }
+        __syncthreads();
 
         // the pass's phase sums for this tile and thread, while the loads are in flight:
         // one thread per pattern adds its fixed-bit-conditioned terms (uniform over the

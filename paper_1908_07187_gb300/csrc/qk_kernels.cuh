@@ -256,6 +256,9 @@ constexpr int kTileMaxOps = 192;
 constexpr int kTileMaxEntries = 512;
 constexpr int kTileMaxPats = 64;
 constexpr int kTileMaxLin = 512;
+// runs of consecutive fixed qubits: S holds 0..4 and eight more bits, which
+// split the rest into at most nine runs
+constexpr int kTileMaxRuns = 12;
 constexpr int kTileMaxMats = 160;
 constexpr int kTileMaxConds = 4;
 constexpr int kTileMaxPhOps = 24;   // TOP_PHASES ops per pass (their sums live in shared memory)
@@ -358,6 +361,10 @@ struct TileParams {
     int nfix;
     int8_t S[16];          // physical qubit of local bit b
     int8_t fixed[40];      // physical bits of the tile index, ascending
+    // the same as runs of consecutive physical bits: tile-index bits [tlo, tlo +
+    // len) land on physical bits [plo, plo + len)
+    int nruns;
+    uint8_t run_tlo[kTileMaxRuns], run_len[kTileMaxRuns], run_plo[kTileMaxRuns];
     int store_arr;
     int n_conds;
     Cond conds[kTileMaxConds];

@@ -279,6 +279,18 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 }
             }
             P.nfix = fb;
+            // runs of consecutive fixed qubits
+            P.nruns = 0;
+            for (int b = 0; b < fb;) {
+                int e = b + 1;
+                while (e < fb && P.fixed[e] == P.fixed[e - 1] + 1) ++e;
+                if (P.nruns >= kTileMaxRuns) return ctx_fail(c, QK_EINVAL, "internal: too many fixed-qubit runs");
+                P.run_tlo[P.nruns] = (uint8_t)b;
+                P.run_len[P.nruns] = (uint8_t)(e - b);
+                P.run_plo[P.nruns] = (uint8_t)P.fixed[b];
+                ++P.nruns;
+                b = e;
+            }
         }
         P.n_conds = (int)conds.size();
         for (int k = 0; k < P.n_conds; ++k) P.conds[k] = conds[k];

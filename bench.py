@@ -85,27 +85,29 @@ def gate_ops(circ):
 DIAGONAL = {"z", "s", "sdg", "t", "tdg", "p", "rz"}
 
 
-def algorithmic_flops(ops, n: int) -> float:
-    """FP32 flops the gate list needs, counted from the gates alone: a non-diagonal
-    2x2 gate with c controls is a complex 2x2 matrix-vector product on 2^(n-c-1)
-    amplitude pairs (4 complex multiplies + 2 complex adds = 28 flops per pair); a
-    diagonal gate is one complex multiply (6 flops) per amplitude it changes; a
-    SWAP is a relabelling (no flops)."""
+def tile_fp32_ops(ops, n: int, tile_launches: float) -> float:
+    """FP32 lane operations the fused tile passes execute for a gate list (an
+    FMA counts as one): an uncontrolled non-diagonal 1-qubit gate is a pivot-form
+    butterfly, 10 operations per amplitude pair (6 FMA, 2 MUL, 2 ADD); a
+    controlled one a full complex 2x2 product on the pairs where the controls
+    hold, 16 per pair; diagonal gates are folded into pending phases (no
+    per-gate arithmetic); each pass ends with one complex factor per amplitude
+    (4 operations).  Flushes at transposes are left out (sign flips are integer
+    work; general phase flushes occur only in the QFT passes), so this is a
+    lower bound."""
     f = 0.0
     for op in ops:
-        c = len(op.controls)
-        if op.kind == "swap":
+        if op.kind == "swap" or op.kind in DIAGONAL:
             continue
-        if op.kind in DIAGONAL:
-            f += 6.0 * 2.0 ** (n - c - 1)
-        else:
-            f += 28.0 * 2.0 ** (n - c - 1)
-    return f
+        c = len(op.controls)
+        f += (10.0 if c == 0 else 16.0) * 2.0 ** (n - c - 1)
+    return f + 4.0 * 2.0 ** n * tile_launches
 
 
-def fp32_peak_tflops(sm_count: int, sm_mhz: float) -> float:
-    """FP32 FMA roofline from unit counts: SMs x 128 FP32 lanes x 2 flops x clock."""
-    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_lane_peak(sm_count: int, sm_mhz: float) -> float:
+    """FP32 lane operations per second: SMs x 128 FP32 lanes x clock (the packed
+    f32x2 forms issue at the same lane rate, measured)."""
+    return sm_count * 128 * sm_mhz * 1e6
 
 
 def peaks():
@@ -191,28 +193,6 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample)
 # ---------------------------------------------------------------------------
-def oracle_state(n: int, circ):
-    """An n-qubit oracle state (every page touched) with the workload's first gate
-    applied, untimed."""
-    import oracle
-
-    st = oracle.OracleState(n)
-    st.psi.fill(0)          # touch every page before timing
-    st.psi[0] = 1
-    st.apply_op(gate_ops(circ)[0])
-    return st
-
-
-def oracle_gates_per_s(st, circ, first: int, count: int):
-    """Time the complex128 oracle, as it stands (one thread), on gate ops
-    first..first+count-1 of the workload.  Returns gates/s."""
-    ops = gate_ops(circ)
-    t0 = time.perf_counter()
-    for op in ops[first:first + count]:
-        st.apply_op(op)
-    return count / (time.perf_counter() - t0)
-
-
 def host_mem_gib():
     try:
         with open("/proc/meminfo") as fh:
@@ -232,61 +212,121 @@ def oracle_size(n: int):
     return m
 
 
+# CPU part numbers of Arm cores (MIDR part field), for hosts whose lscpu is missing
+ARM_PARTS = {"0xd0c": "Neoverse-N1", "0xd40": "Neoverse-V1", "0xd49": "Neoverse-N2", "0xd4f": "Neoverse-V2",
+             "0xd8e": "Neoverse-N3", "0xd84": "Neoverse-V3"}
+
+
 def host_info():
-    """The host the oracle is timed on: logical CPUs and the CPU model."""
+    """The host the oracle is timed on: logical CPUs and the CPU model (lscpu's
+    model name, else /proc/cpuinfo's model name or Arm CPU part)."""
+    import platform
+
     model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    part = ""
     try:
         with open("/proc/cpuinfo") as fh:
             for line in fh:
                 key = line.split(":", 1)[0].strip().lower()
-                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                if not model and key == "model name":
                     model = line.split(":", 1)[1].strip()
-                    break
+                if key == "cpu part" and not part:
+                    part = line.split(":", 1)[1].strip().lower()
     except OSError:
         pass
-    import platform
+    if not model and part:
+        model = ARM_PARTS.get(part, f"Arm CPU part {part}")
+    return {"nproc": os.cpu_count(), "cpu": model or platform.machine(), "arch": platform.machine()}
 
-    return {"nproc": os.cpu_count(), "cpu": model or platform.processor() or platform.machine()}
+
+def oracle_gate_rate(m: int, circ, first: int, count: int, openmp: bool, budget_s: float = 1e9):
+    """Time the complex128 oracle on gate ops first..first+count-1 of an m-qubit
+    workload circuit (gate op 0 applied untimed, which also touches every page of
+    the state), stopping early once budget_s has passed.  Returns (gates, s)."""
+    import oracle
+
+    st = oracle.OracleState(m, openmp=openmp)
+    ops = gate_ops(circ)
+    st.apply_op(ops[0])
+    t0 = time.perf_counter()
+    done = 0
+    for op in ops[first:first + count]:
+        st.apply_op(op)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return done, time.perf_counter() - t0
 
 
-def cpu_baseline(n: int, circ, count: int = 1):
-    m = oracle_size(n)
-    c = circ if m == n else workload(m, 2)
-    st = oracle_state(m, c)
-    gps = oracle_gates_per_s(st, c, 1, count) * 2.0 ** (m - n)   # per-gate cost scales with 2^n
-    sample = f"gate ops 2..{count + 1} of the {m}-qubit layered circuit (gate 1 untimed) on the complex128 oracle, 1 thread"
-    if m != n:
-        sample += f", scaled by 2^{m - n} to {n} qubits"
-    return {"value": gps, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "host": host_info()}
+def cpu_baseline(n: int, circ):
+    """The oracle as it stands on the host: one thread on 20 gates of the
+    layered circuit at min(n, 26) qubits (per-gate cost scales with 2^n, so the
+    rate is scaled to n), and the all-core build on the n-qubit state (or the
+    largest that fits in host RAM) for up to about 10 s of gates."""
+    hi = host_info()
+    m1 = min(n, 26)
+    g1, t1 = oracle_gate_rate(m1, workload(m1, 2), 1, 20, openmp=False)
+    single = g1 / t1 * 2.0 ** (m1 - n)
+    m2 = oracle_size(n)
+    g2, t2 = oracle_gate_rate(m2, circ if m2 == n else workload(m2, 2), 1, 200, openmp=True, budget_s=10.0)
+    allc = g2 / t2 * 2.0 ** (m2 - n)
+    sample = (f"gate ops 2..{g2 + 1} of the {m2}-qubit layered circuit (gate 1 untimed) on the complex128 oracle's "
+              f"all-core build, {hi['nproc']} threads, {t2:.1f} s")
+    if m2 != n:
+        sample += f", scaled by 2^{m2 - n} to {n} qubits"
+    return {"value": allc, "unit": UNIT, "cores": hi["nproc"], "kind": "oracle", "sample": sample,
+            "single_thread": {"value": single, "unit": UNIT, "cores": 1, "ms_per_gate_at_n": 1000.0 / single,
+                              "sample": f"gate ops 2..21 of the {m1}-qubit layered circuit, 1 thread, {t1:.1f} s"
+                                        + (f", scaled by 2^{m1 - n} to {n} qubits" if m1 != n else "")},
+            "host": hi}
 
 
 def run_reference(args):
+    """The CPU oracle arm: the complex128 oracle (all-core build) on the host,
+    each step two gate ops of the n-qubit layered circuit (or of the largest
+    that fits in host RAM, scaled by the state size), timed as run."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    import oracle
+
+    hi = host_info()
     n = args.n
-    m = oracle_size(min(n, 27))   # one step stays near a second of CPU time
+    m = oracle_size(n)
     circ = workload(m, 2)
-    st = oracle_state(m, circ)
-    per_step = 1
-    vals = []
-    pos = 1
+    ops = gate_ops(circ)
+    st = oracle.OracleState(m, openmp=True)
+    st.apply_op(ops[0])             # untimed: touches every page
+    per_step = 2
+    ms, pos = [], 1
     for s in range(args.warmup + args.steps):
-        gps = oracle_gates_per_s(st, circ, pos, per_step) * 2.0 ** (m - n)
+        t0 = time.perf_counter()
+        for op in ops[pos:pos + per_step]:
+            st.apply_op(op)
+        dt = time.perf_counter() - t0
         pos += per_step
         if s >= args.warmup:
-            vals.append(gps)
-    value = statistics.median(vals)
-    sample = f"{per_step} gate per step of the {m}-qubit layered circuit on the complex128 oracle, 1 thread"
+            ms.append(1000.0 * dt)
+    ms_step = statistics.median(ms)
+    value = per_step / (ms_step / 1000.0) * 2.0 ** (m - n)
+    sample = f"{per_step} gate ops per step of the {m}-qubit layered circuit on the complex128 oracle, {hi['nproc']} threads"
     if m != n:
-        sample += f", scaled by 2^{m - n} to {n} qubits"
+        sample += f", rate scaled by 2^{m - n} to {n} qubits (ms_per_step is as timed at {m} qubits)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * per_step / value,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": {"workload": f"layered U3/CZ-brickwork 500 gates + QFT({n}) + measure all, {n} qubits",
-                       "n_qubits": n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-                             "host": host_info()},
+                       "n_qubits": n, "gate_ops_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": hi["nproc"], "kind": "oracle", "sample": sample,
+                             "host": hi},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -636,38 +676,39 @@ def main():
         plain = {"value": n_gates / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms}
         pctx.close()
 
-    # roofline for the kernel class with the largest device-time share
+    # roofline for the kernel class with the largest device-time share: HBM,
+    # the algorithmic bytes of one launch (a tile pass reads and writes the state
+    # once: 2^n x 8 B x 2) over the launch's average CUDA-event time
     top = max(prof, key=lambda k: prof[k]["ms"])
     rec = prof[top]
     peak, peak_kind = peaks()
-    achieved = (rec["bytes"] / rec["launches"]) / (rec["ms"] / rec["launches"] / 1000.0) / 1e9 if rec["launches"] else 0
+    per_launch_s = rec["ms"] / rec["launches"] / 1000.0 if rec["launches"] else 0.0
+    alg_bytes = rec["bytes"] / rec["launches"] if rec["launches"] else 0.0
+    achieved = alg_bytes / per_launch_s / 1e9 if per_launch_s else 0.0
     traffic = recorded_traffic(top, n)
     tot_ms = sum(v["ms"] for v in prof.values())
-    roofline_hbm = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": top,
-                    "peak_kind": peak_kind, "launches_per_step": rec["launches"] / args.steps,
-                    "share_of_device_time": round(rec["ms"] / tot_ms, 4) if tot_ms else None,
-                    "alg_bytes_per_launch": rec["bytes"] / rec["launches"] if rec["launches"] else None}
-    roofline = roofline_hbm
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": top,
+                "peak_kind": f"{peak_kind} (copy bandwidth, MEASURED_PEAKS.json hbm_gbs)",
+                "launches_per_step": rec["launches"] / args.steps,
+                "share_of_device_time": round(rec["ms"] / tot_ms, 4) if tot_ms else None,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": round(1000.0 * per_launch_s, 4)}
+    roofline_fp32 = None
     if top == "tile":
-        # the fused pass is bound by FP32 issue, not HBM: roofline against the FMA peak
+        # the same passes against the FP32 lane rate, counting what the kernel executes
         sm_count = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        sm_mhz = 2070.0
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-                sm_mhz = float(json.load(fh).get("sm_max_mhz", sm_mhz))
-        except Exception:
-            pass
-        flops_step = algorithmic_flops(gops, n)
-        tile_s_step = rec["ms"] / args.steps / 1000.0
-        alu_peak = fp32_peak_tflops(sm_count, sm_mhz)
-        alu_ach = flops_step / tile_s_step / 1e12
-        roofline = {"bound": "alu", "achieved": round(alu_ach, 2), "peak": round(alu_peak, 1), "unit": "TFLOP/s",
-                    "frac": round(alu_ach / alu_peak, 4), "traffic": traffic, "kernel": top,
-                    "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz",
-                    "alg_flops_per_launch": flops_step / rec["launches"] * args.steps,
-                    "launches_per_step": rec["launches"] / args.steps,
-                    "share_of_device_time": roofline_hbm["share_of_device_time"]}
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        launches_step = rec["launches"] / args.steps
+        ops_step = tile_fp32_ops(gops, n, launches_step)
+        lane_peak = fp32_lane_peak(sm_count, sm_mhz)
+        rate = ops_step / (rec["ms"] / args.steps / 1000.0)
+        roofline_fp32 = {"bound": "alu", "achieved": round(rate / 1e12, 3), "peak": round(lane_peak / 1e12, 3),
+                         "unit": "T FP32 lane-ops/s", "frac": round(rate / lane_peak, 4),
+                         "ops_per_step": ops_step,
+                         "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock "
+                                      "sampled during the timed region)",
+                         "count": "10 per amplitude pair per uncontrolled non-diagonal gate, 16 per acting pair per "
+                                  "controlled one, 4 per amplitude per pass (final phase and scale); lower bound"}
 
     kitaev = None
     if not args.no_kitaev:
@@ -701,7 +742,7 @@ def main():
             "gpu_launches": counters["launches"],
             "state_passes_per_step": counters["state_passes"] / args.steps,
             "roofline": roofline,
-            "roofline_hbm": roofline_hbm,
+            "roofline_fp32": roofline_fp32,
             # what one-pass-per-gate execution would have to stream for the same gates/s
             "gate_equivalent_bandwidth": {
                 "GBps": round(value * 2 * 8 * (1 << n) / 1e9, 1),

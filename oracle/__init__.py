@@ -26,25 +26,29 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qk_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 
-def build(force: bool = False) -> str:
-    """Compile qk_oracle.c into liboracle.so next to it (gcc, portable flags)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile qk_oracle.c into liboracle.so next to it (gcc, portable flags).
+    With openmp=True, the all-core build liboracle_omp.so (-fopenmp: the gate
+    loop's groups split across the host's cores; nothing else differs), used
+    only to time the oracle on every core."""
+    out = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC"] +
+                              (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
+def lib(openmp: bool = False):
     with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build())
+        if openmp not in _libs:
+            L = ctypes.CDLL(build(openmp=openmp))
             dp, ip, up = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64)
             L.orc_apply_unitary.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip, dp, ip, ctypes.c_int]
             L.orc_apply_perm.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip, up, ip, ctypes.c_int]
@@ -57,8 +61,8 @@ def lib():
                                            ctypes.c_int]
             L.orc_norm2.argtypes = [dp, ctypes.c_int]
             L.orc_norm2.restype = ctypes.c_double
-            _lib = L
-    return _lib
+            _libs[openmp] = L
+    return _libs[openmp]
 
 
 def _ints(xs: Sequence[int]):
@@ -130,8 +134,9 @@ def gate_matrix(kind: str, params: Sequence[float] = ()) -> np.ndarray:
 class OracleState:
     """A 2^n complex128 state vector plus a classical bit register."""
 
-    def __init__(self, n: int, n_cbits: int = 0, psi: Optional[np.ndarray] = None):
+    def __init__(self, n: int, n_cbits: int = 0, psi: Optional[np.ndarray] = None, openmp: bool = False):
         self.n = n
+        self._openmp = openmp
         if psi is None:
             self.psi = np.zeros(1 << n, dtype=np.complex128)
             self.psi[0] = 1.0
@@ -165,7 +170,7 @@ class OracleState:
         if u.shape != (1 << k, 1 << k):
             raise ValueError("matrix shape does not match target count")
         flat = np.ascontiguousarray(u.view(np.float64).reshape(-1))
-        rc = lib().orc_apply_unitary(_dptr(self.psi.view(np.float64)), self.n, k, _ints(targets),
+        rc = lib(self._openmp).orc_apply_unitary(_dptr(self.psi.view(np.float64)), self.n, k, _ints(targets),
                                      _dptr(flat), _ints(controls), len(controls))
         if rc != 0:
             raise ValueError("oracle rejected unitary arguments")

@@ -444,3 +444,16 @@ def test_kitaev_op_list_matches_the_stage_by_stage_oracle(N, a):
     ref = oracle.run_circuit(circ)
     assert [int(x) for x in ref.cbits] == bits
     np.testing.assert_allclose(ref.psi, st.psi, atol=1e-13)
+
+
+def test_all_core_oracle_build_is_bit_identical():
+    """The OpenMP build of the oracle (used only to time it on every host core)
+    splits the gate loop's independent groups across threads; each group's
+    arithmetic is unchanged, so the states agree bit for bit."""
+    circ = workloads.layered_circuit(14, seed=5, n_gates=90, qft=True)
+    a = oracle.OracleState(14)
+    b = oracle.OracleState(14, openmp=True)
+    for op in circ.ops:
+        a.apply_op(op)
+        b.apply_op(op)
+    assert np.array_equal(a.psi, b.psi)

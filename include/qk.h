@@ -233,8 +233,18 @@ qk_status qk_device_state(qk_ctx *ctx, void **dptr, size_t *bytes);
 /* Run every queued gate (fused mode); stream-ordered, does not wait. */
 qk_status qk_flush(qk_ctx *ctx);
 
-/* Flush and wait until all work on the context's stream has finished. */
+/* Flush and wait until all work on the context's stream has finished.  Returns
+ * QK_ETIMEOUT (and clears the condition) if a kernel's bounded device-side wait
+ * gave up since the last qk_sync; the context stays usable, the state is not. */
 qk_status qk_sync(qk_ctx *ctx);
+
+/* Self-test of that failure path (the paper has no counterpart): enqueues one
+ * kernel that waits, with the same bounded mbarrier wait the tensor-core pass
+ * uses but a limit of about a millisecond, on a barrier nothing arrives at.  The
+ * wait runs out, the kernel records the timeout in the context's error flag and
+ * returns; the next qk_sync returns QK_ETIMEOUT.  Nothing faults and the state
+ * is untouched.  Errors: QK_ECUDA (launch failed). */
+qk_status qk_selftest_timeout(qk_ctx *ctx);
 
 /* Number of qubits / cbits of the context. */
 int qk_num_qubits(const qk_ctx *ctx);

@@ -55,13 +55,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait on an mbarrier phase; false after kWaitLimit tries
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+// bounded wait on an mbarrier phase; false after `limit` tries
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit = kWaitLimit) {
+    for (uint32_t i = 0; i < limit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (i > 32) __nanosleep(64);
     }
     return false;
+}
+
+// Self-test of the timeout path: one thread waits on a fresh barrier that
+// nothing arrives at, gives up after `limit` tries and records it in err.
+__global__ void k_wait_selftest(int *err, uint32_t limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = smem_u32(&bar);
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(b, 0, limit)) atomicExch(err, 1);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
@@ -248,6 +259,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
+cudaError_t launch_wait_selftest(int *err, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(err, 1u << 14);   // about a millisecond
+    return cudaGetLastError();
+}
+
 cudaError_t launch_block_tc(void *psi, int n, const float *bh, const float *bl, int *err, int sms, cudaStream_t s) {
     if (n < 5) return cudaErrorInvalidValue;
     if (((uintptr_t)psi & 15) != 0) return cudaErrorInvalidValue;
@@ -263,11 +279,16 @@ cudaError_t launch_block_tc(void *psi, int n, const float *bh, const float *bl, 
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
         CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
+    // the shared-memory attribute is set once per device
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t ed = cudaGetDevice(&dev);
+    if (ed != cudaSuccess) return ed;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
         cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr_set[dev] = true;
     }
     const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
     uint64_t grid = n_tiles < (uint64_t)(2 * sms) ? n_tiles : (uint64_t)(2 * sms);

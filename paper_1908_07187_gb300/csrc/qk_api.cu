@@ -1011,6 +1011,13 @@ qk_status qk_sync(qk_ctx *c) {
     return QK_OK;
 }
 
+qk_status qk_selftest_timeout(qk_ctx *c) {
+    if (!c) return QK_EINVAL;
+    NOT_WHILE_CAPTURING(c, "selftest_timeout");
+    CUDA_TRY(c, qk::launch_wait_selftest(c->d_err, c->stream));
+    return QK_OK;
+}
+
 qk_status qk_capture_begin(qk_ctx *c) {
     if (!c) return QK_EINVAL;
     NOT_WHILE_CAPTURING(c, "capture_begin");

@@ -413,6 +413,8 @@ cudaError_t launch_kitaev_update(int prec, const void *psi, void *out, const Kit
 // physical qubits 0..4; bh/bl are the 64 x 64 split real embedding (row = output
 // column); err receives 1 if a bounded wait gave up.
 cudaError_t launch_block_tc(void *psi, int n, const float *bh, const float *bl, int *err, int sms, cudaStream_t s);
+// one bounded mbarrier wait that runs out; sets *err (the timeout path's self-test)
+cudaError_t launch_wait_selftest(int *err, cudaStream_t s);
 cudaError_t launch_set_basis(int prec, void *psi, uint64_t index, cudaStream_t s);
 cudaError_t launch_relabel(int prec, const void *in, void *out, const RelabelArgs &a, int sms,
                            cudaStream_t s);

@@ -101,6 +101,7 @@ _SIGS = {
     "qk_device_state": ([_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "qk_flush": ([_P], ctypes.c_int),
     "qk_sync": ([_P], ctypes.c_int),
+    "qk_selftest_timeout": ([_P], ctypes.c_int),
     "qk_num_qubits": ([_P], ctypes.c_int),
     "qk_num_cbits": ([_P], ctypes.c_int),
     "qk_get_counters": ([_P, _U64P, _U64P, _U64P], ctypes.c_int),
@@ -322,6 +323,10 @@ class Context:
 
     def sync(self):
         self._check(_lib.qk_sync(self._h))
+
+    def selftest_timeout(self):
+        """Enqueue the bounded-wait self-test; the next sync raises QK_ETIMEOUT."""
+        self._check(_lib.qk_selftest_timeout(self._h))
 
     def capture_begin(self):
         self._check(_lib.qk_capture_begin(self._h))

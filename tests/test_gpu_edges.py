@@ -86,3 +86,26 @@ def test_rejected_gate_leaves_the_state_unchanged(qk):
         assert e.value.status == qk.QK_EINVAL
     np.testing.assert_array_equal(ctx.get_state(), psi)
     ctx.close()
+
+
+def test_bounded_wait_timeout_is_reported_and_context_stays_usable(qk):
+    """The bounded device-side wait gives up (the self-test waits on a barrier
+    nothing arrives at), qk_sync reports QK_ETIMEOUT once, and the context keeps
+    working: the state is untouched and later gates are correct."""
+    import oracle
+
+    n = 6
+    psi = workloads.random_state(n, 71)
+    ctx = qk.Context("c64", "fused")
+    ctx.add_qubits(n)
+    ctx.set_state(psi)
+    ctx.selftest_timeout()
+    with pytest.raises(qk.QKError) as e:
+        ctx.sync()
+    assert e.value.status == qk.QK_ETIMEOUT
+    ctx.sync()                                   # the condition was cleared
+    ctx.apply_gate("h", [2])
+    ref = oracle.OracleState(n, psi=psi)
+    ref.apply_matrix(oracle.GATES_1Q["h"], [2])
+    np.testing.assert_allclose(ctx.get_state(), ref.psi, atol=1e-5)
+    ctx.close()

@@ -410,6 +410,63 @@ def test_fused_two_qubit_diagonals_every_pattern(qk, targets):
     ctx.close()
 
 
+@pytest.mark.parametrize("b", [16, 18, 20])
+def test_kitaev_large_registers_bits_exact_against_oracle(qk, b):
+    """Order finding at the b = 16..20-bit sizes of the benchmark configuration
+    (17..21 qubits; the Abstract's 21-qubit run is the b = 20 shape): the fused
+    stage calls and their CUDA-graph replay give the oracle's measured bits
+    exactly and its final state within the complex64 bound."""
+    N, a = workloads.kitaev_parameters(b, seed=3)
+    circ = workloads.kitaev_circuit(N, a, seed=5)
+    ref = oracle.run_circuit(circ)
+    ctx = qk.Context("c64", "fused")
+    ctx.add_qubits(circ.n_qubits)
+    ctx.add_cbits(circ.n_cbits)
+    qk.run_kitaev_fused(ctx, circ)
+    assert list(ctx.read_cbits()) == [int(x) for x in ref.cbits]
+    check_state(ctx.get_state(), ref.psi, "c64")
+    ctx.sync()
+    ctx.capture_begin()
+    ctx.reset()
+    qk.run_kitaev_fused(ctx, circ)
+    g = ctx.capture_end()
+    ctx.write_cbits(0, [0] * circ.n_cbits)
+    g.launch()
+    assert list(ctx.read_cbits()) == [int(x) for x in ref.cbits]
+    check_state(ctx.get_state(), ref.psi, "c64")
+    g.close()
+    ctx.close()
+
+
+@pytest.mark.parametrize("qubits", [[0], [7], [21], [3, 17]])
+def test_measurement_probability_within_1e9_of_oracle(qk, qubits):
+    """The complex64 measurement sums (compensated FP32 per thread, FP64 across)
+    against the oracle's FP64 sums on the same complex64 amplitudes: a uniform
+    1e-9 below the oracle's P0 reads 0 and 1e-9 above reads 1, for every decision
+    of a sequential measurement, on a 22-qubit state whose P0 values sit near 1/2."""
+    n = 22
+    psi = workloads.random_state(n, 404).astype(np.complex64)
+    ref = oracle.OracleState(n, psi=psi.astype(np.complex128))
+    # the oracle's P0 of each decision in turn, each taken on the collapsed state
+    base_u = [0.3] * len(qubits)
+    probe = oracle.OracleState(n, psi=psi.astype(np.complex128))
+    p0s = []
+    for j, q in enumerate(qubits):
+        p0s.append(probe.prob0(q))
+        probe.measure([q], [base_u[j]])
+    assert all(abs(p - 0.5) < 0.01 for p in p0s)
+    for j in range(len(qubits)):
+        for delta, want in ((-1e-9, 0), (1e-9, 1)):
+            us = list(base_u)
+            us[j] = p0s[j] + delta
+            ctx = new_ctx(qk, n, "c64", "plain", psi)
+            v = ctx.measure(qubits, us)
+            bit = (v >> (len(qubits) - 1 - j)) & 1
+            assert bit == want, (qubits, j, delta, p0s[j])
+            ctx.close()
+    _ = ref
+
+
 @pytest.mark.parametrize("b,prec", [(4, "c64"), (6, "c128"), (12, "c64"), (14, "c64")])
 def test_fused_kitaev_stage_matches_oracle_and_generic(qk, b, prec):
     N, a = (15, 7) if b == 4 else workloads.kitaev_parameters(b, seed=3)

@@ -268,20 +268,26 @@ qk_status qk_capture_end(qk_ctx *ctx, qk_graph **out);
 qk_status qk_graph_launch(qk_graph *g);
 qk_status qk_graph_destroy(qk_graph *g);
 
-/* Batched small circuits (no counterpart in the paper; it serves many small
- * requests with one launch).  A batch holds up to thousands of independent
- * circuits of 1..13 qubits (complex64, up to 64 cbits each); each runs entirely
- * in one CTA's shared memory, from |0...0> and cbits 0, with the same op
- * semantics as a context: built-in 1-target gates with quantum controls and
- * classical conditions (qk_batch_apply_gate), the controlled mul-mod oracle of
- * Appendix A (qk_batch_apply_mulmod, register <= 16 qubits), and sequential
- * single-qubit measurement into cbits (qk_batch_measure).  qk_batch_run uploads
- * the programs and launches (one launch per distinct qubit count) on the batch's
- * stream without waiting; qk_batch_done polls; qk_batch_read waits and copies a
- * circuit's cbits and (if stored) final state.  Add ops to the most recently
- * added circuit.  qk_batch_clear waits for a previous run and empties the batch.
- * Errors: QK_EINVAL (sizes, qubit lists, params), QK_ENOTBIJECTIVE, QK_ESTATE
- * (op before any circuit), QK_ENOMEM, QK_ECUDA; message in qk_batch_last_error. */
+/* Batched circuits (no counterpart in the paper; it serves many independent
+ * circuits with few launches).  A batch holds up to thousands of circuits of
+ * 1..24 qubits (complex64, up to 64 cbits each), each from |0...0> and cbits 0.
+ * A circuit of 1..13 qubits runs entirely in one CTA's shared memory with the
+ * same op semantics as a context: built-in 1-target gates with quantum controls
+ * and classical conditions (qk_batch_apply_gate), the controlled mul-mod oracle
+ * of Appendix A (qk_batch_apply_mulmod, register <= 16 qubits), and sequential
+ * single-qubit measurement into cbits (qk_batch_measure).  A circuit of 14..24
+ * qubits takes built-in 1-target gates with at most one quantum control and no
+ * classical condition (QK_EINVAL otherwise); its state stays in device memory,
+ * qk_batch_run plans it into fused tile passes (on the host's cores) and runs
+ * pass k of every such circuit in one batched launch.  qk_batch_run uploads the
+ * programs and launches (one launch per distinct small-circuit size, one per
+ * pass index of the large circuits) on the batch's stream without waiting;
+ * qk_batch_done polls; qk_batch_read waits and copies a circuit's cbits and
+ * final state (always kept for large circuits, for small ones if stored).  Add
+ * ops to the most recently added circuit.  qk_batch_clear waits for a previous
+ * run and empties the batch.  Errors: QK_EINVAL (sizes, qubit lists, params),
+ * QK_ENOTBIJECTIVE, QK_ESTATE (op before any circuit), QK_ENOMEM, QK_ECUDA;
+ * message in qk_batch_last_error. */
 typedef struct qk_batch qk_batch;
 qk_status qk_batch_create(qk_batch **out, void *cuda_stream);
 qk_status qk_batch_destroy(qk_batch *b);
@@ -316,6 +322,9 @@ qk_status qk_batch_read(qk_batch *b, int circuit, uint8_t *cbits, int ncb, void 
 /* All circuits' cbits, concatenated in circuit order (sum of their cbit counts). */
 qk_status qk_batch_read_all_cbits(qk_batch *b, uint8_t *out, size_t n);
 int qk_batch_num_circuits(const qk_batch *b);
+/* Host planning time (ms) of the large circuits and the number of batched tile
+ * launches of the last qk_batch_run. */
+qk_status qk_batch_stats(const qk_batch *b, double *plan_ms, int *tile_launches);
 const char *qk_batch_last_error(const qk_batch *b);
 
 /* Counters since creation or the last reset_counters: kernel launches, passes

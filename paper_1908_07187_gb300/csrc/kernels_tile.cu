@@ -445,13 +445,6 @@ __device__ __forceinline__ void pair_neg(Regs &v, int code) {
     }
 }
 
-// fixed-bit masks and the tile base in the offset width (32 bits while n <= 32)
-template <typename Off>
-__device__ __forceinline__ Off ld_mask(const uint64_t *p) {
-    if constexpr (sizeof(Off) == 4) return __ldg(reinterpret_cast<const uint32_t *>(p));  // low word
-    else return __ldg(reinterpret_cast<const unsigned long long *>(p));
-}
-
 template <typename Off>
 __device__ __forceinline__ bool op_applies(const TileOp &op, int tbits, Off base, unsigned condok) {
     if ((tbits & op.tmask) != op.tval) return false;
@@ -502,7 +495,8 @@ __device__ __forceinline__ void store_all(float2 *dst, const Offsets<Off> &o, Re
 
 // Physical index of a tile's base (its local qubits 0): the tile index's bits
 // deposited on the fixed qubits, one run of consecutive qubits at a time.
-__device__ __forceinline__ uint64_t tile_base(const TileParams &P, uint64_t tile) {
+template <typename Head>
+__device__ __forceinline__ uint64_t tile_base(const Head &P, uint64_t tile) {
     uint64_t b = 0;
 #pragma unroll
     for (int r = 0; r < kTileMaxRuns; ++r)
@@ -592,17 +586,35 @@ __device__ __forceinline__ void general_op(Regs &v, DevPending &pd, const TileOp
     }
 }
 
-template <typename Off>
-__global__ void __launch_bounds__(kTileThreads, 2)
-    k_tile(float2 *__restrict__ psi, const __grid_constant__ TileParams P, const TileEntries *__restrict__ tab,
-           const uint8_t *__restrict__ cbits) {
+// Where a pass program lives: in the kernel parameters (one state), or in
+// device pools (a batched launch over many circuits).
+struct ParamProg {
+    const TileParams &P;
+    __device__ __forceinline__ const TileHead &head() const { return P; }
+    __device__ __forceinline__ const TileOp &op(int i) const { return P.ops[i]; }
+    __device__ __forceinline__ const LayerGate &lg(int i) const { return P.lg[i]; }
+    __device__ __forceinline__ const LinTerm &lin(int i) const { return P.lin[i]; }
+};
+struct PoolProg {
+    const TileProg &h;
+    const TileOp *ops;
+    const LayerGate *lgs;
+    const LinTerm *lins;
+    __device__ __forceinline__ const TileProg &head() const { return h; }
+    __device__ __forceinline__ const TileOp &op(int i) const { return ops[h.op0 + i]; }
+    __device__ __forceinline__ const LayerGate &lg(int i) const { return lgs[h.lg0 + i]; }
+    __device__ __forceinline__ const LinTerm &lin(int i) const { return lins[h.lin0 + i]; }
+};
+
+// One tile of one pass: load, run the program, final flush, store.
+template <typename Off, typename Prog>
+__device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ psi, uint64_t tile,
+                                          const uint8_t *__restrict__ cbits) {
+    const auto &P = pr.head();
     // 2 x 2^13 floats (64 KiB) for transposes, then per thread six pending words
-    // and one word per TOP_PHASES op, then one word per pattern
     extern __shared__ __align__(16) float smf[];
     float *sre = smf, *sim = smf + (1 << kTileQubits);
     uint32_t *spd = reinterpret_cast<uint32_t *>(smf + (2 << kTileQubits));     // pending sums
-    uint32_t *sph = spd + 6 * kTileThreads;                                      // phase-op sums
-    uint32_t *spat = sph + P.nphops * kTileThreads;                              // pattern sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int tbits = (warp << 5) | lane;
     // lanes run over local qubits 0..4 in the load and store arrangements
@@ -611,10 +623,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     for (int j = 0; j < 5; ++j)
         if ((lane >> j) & 1) lane_off += 1ull << P.S[j];
 
-    // one tile per CTA (a grid-stride loop would keep the tile's addressing state
-    // live across iterations and push the kernel into spills)
     {
-        const uint64_t tile = blockIdx.x;
         const Off base = (Off)tile_base(P, tile);
 
         // load in ARR_IO: lanes = local 0..4, registers = local 5..9, warps = local 10..12
@@ -652,43 +661,16 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         }
         __syncthreads();
 
-        // the pass's phase sums for this tile and thread, while the loads are in flight:
-        // one thread per pattern adds its fixed-bit-conditioned terms (uniform over the
-        // tile), then every thread adds the patterns whose thread-bit condition it meets
-        if (P.nphops) {
-            for (int q = threadIdx.x; q < P.npats; q += kTileThreads) {
-                const PhasePattern pt = tab->p[q];
-                uint32_t sum = pt.turns;
-                const int ende = pt.first + pt.count;
-                for (int e = pt.first; e < ende; ++e) {
-                    const Off gm = ld_mask<Off>(&tab->e[e].gmask), gv = ld_mask<Off>(&tab->e[e].gval);
-                    const uint32_t tu = __ldg(&tab->e[e].turns);
-                    sum += ((base & gm) == gv) ? tu : 0u;
-                }
-                spat[q] = sum;
-            }
-            __syncthreads();
-            for (int slot = 0; slot < P.nphops; ++slot) {
-                uint32_t acc = 0;
-                const int endp = P.phop[slot][0] + P.phop[slot][1];
-                for (int q = P.phop[slot][0]; q < endp; ++q) {
-                    const PhasePattern &pt = P.pats[q];
-                    acc += ((tbits & pt.tmask) == pt.tval) ? spat[q] : 0u;
-                }
-                sph[slot * kTileThreads + threadIdx.x] = acc;
-            }
-        }
-
         DevPending pd;
         pd.p = spd + threadIdx.x;
         pd.reset();
         int cur = ARR_IO;
         const uint32_t tidx = (uint32_t)tile;
         for (int i = 0; i < P.nops; ++i) {
-            const TileOp &op = P.ops[i];
+            const TileOp &op = pr.op(i);
             switch (op.kind) {
                 case TOP_U2L: {
-                    const LayerGate *lg = &P.lg[op.first];
+                    const LayerGate *lg = &pr.lg(op.first);
                     const int bits = op.k;
                     if (bits & 1) layer_gate<0>(v, pd, *lg++);
                     if (bits & 2) layer_gate<1>(v, pd, *lg++);
@@ -704,8 +686,8 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                     uint32_t acc = 0;
                     const int end = op.first + op.count;
                     for (int e = op.first; e < end; ++e) {
-                        const LinTerm &L = P.lin[e];
-                        const bool ok = ((tbits & L.tmask) == L.tval) && (L.fbit == 0xff || ((tidx >> L.fbit) & 1u));
+                        const LinTerm &L = pr.lin(e);
+                        const bool ok = ((tbits & L.tmask) == L.tval) && ((tidx & L.fmask) == L.fval);
                         acc += ok ? L.turns : 0u;
                     }
                     if (acc) {
@@ -723,16 +705,6 @@ __global__ void __launch_bounds__(kTileThreads, 2)
                     transpose(v, sre, sim, cur, op.k, lane, warp);
                     cur = op.k;
                     break;
-                case TOP_PHASES: {
-                    const uint32_t acc = sph[op.count2 * kTileThreads + threadIdx.x];
-                    if (op.rval) {
-                        pd.add(5, acc);
-                        pd.add(op.k, 0u - acc);
-                    } else {
-                        pd.add(op.k, acc);
-                    }
-                    break;
-                }
                 default:
                     general_op<Off>(v, pd, op, tbits, base, condok);
                     break;
@@ -786,20 +758,34 @@ __global__ void __launch_bounds__(kTileThreads, 2)
     }
 }
 
-__global__ void k_tile_entries(const __grid_constant__ TileEntries E, int ne, int np, TileEntries *__restrict__ dst) {
-    for (int i = threadIdx.x; i < ne; i += blockDim.x) dst->e[i] = E.e[i];
-    for (int i = threadIdx.x; i < np; i += blockDim.x) dst->p[i] = E.p[i];
+// one tile per CTA (a grid-stride loop would keep the tile's addressing state
+// live across iterations and push the kernel into spills)
+template <typename Off>
+__global__ void __launch_bounds__(kTileThreads, 2)
+    k_tile(float2 *__restrict__ psi, const __grid_constant__ TileParams P, const uint8_t *__restrict__ cbits) {
+    tile_body<Off>(ParamProg{P}, psi, blockIdx.x, cbits);
+}
+
+// Batched: CTA b finds its program by binary search in first[] (uniform over
+// the CTA) and runs that program's tile b - first[c] on the program's state.
+__global__ void __launch_bounds__(kTileThreads, 2)
+    k_tile_batch(const TileProg *__restrict__ progs, const uint32_t *__restrict__ first, int n_progs,
+                 const TileOp *__restrict__ ops, const LayerGate *__restrict__ lg, const LinTerm *__restrict__ lin) {
+    int lo = 0, hi = n_progs - 1;
+    const uint32_t b = blockIdx.x;
+    while (lo < hi) {  // the last c with first[c] <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&first[mid]) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const TileProg &h = progs[lo];
+    tile_body<uint32_t>(PoolProg{h, ops, lg, lin}, h.psi, b - __ldg(&first[lo]), nullptr);
 }
 
 template <typename Off>
-cudaError_t launch_tile_t(void *psi, const TileParams &p, const TileEntries *entries, const uint8_t *cbits,
-                          cudaStream_t s) {
-    // transposes (2^13 complex64), pending sums (6 words per thread), phase-op sums
-    // (one word per thread each), pattern sums
-    constexpr int smem_max = ((int)(2 * sizeof(float)) << kTileQubits) + (6 + kTileMaxPhOps) * kTileThreads * 4 +
-                             kTileMaxPats * 4;
-    const int smem = ((int)(2 * sizeof(float)) << kTileQubits) + (6 + p.nphops) * kTileThreads * 4 +
-                     (p.nphops ? p.npats * 4 : 0);
+cudaError_t launch_tile_t(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s) {
+    // transposes (2^13 complex64) and pending sums (6 words per thread)
+    constexpr int smem = ((int)(2 * sizeof(float)) << kTileQubits) + 6 * kTileThreads * 4;
     // the shared-memory attribute is set once per device
     static bool attr_set[64] = {false};
     int dev = 0;
@@ -807,28 +793,41 @@ cudaError_t launch_tile_t(void *psi, const TileParams &p, const TileEntries *ent
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
-        e = cudaFuncSetAttribute(k_tile<Off>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+        e = cudaFuncSetAttribute(k_tile<Off>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
     if (p.n_tiles == 0 || p.n_tiles > (1ull << 31) - 1) return cudaErrorInvalidValue;
-    k_tile<Off><<<(unsigned)p.n_tiles, kTileThreads, smem, s>>>((float2 *)psi, p, entries, cbits);
+    k_tile<Off><<<(unsigned)p.n_tiles, kTileThreads, smem, s>>>((float2 *)psi, p, cbits);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_tile(void *psi, const TileParams &p, const TileEntries *entries, const uint8_t *cbits,
-                        cudaStream_t s) {
-    // 32-bit element offsets inside a tile reach 2^32 amplitudes
-    if (p.n <= 32) return launch_tile_t<uint32_t>(psi, p, entries, cbits, s);
-    return launch_tile_t<uint64_t>(psi, p, entries, cbits, s);
+cudaError_t launch_tile_batch(const TileProg *progs, const uint32_t *first, int n_progs, uint32_t n_ctas,
+                              const TileOp *ops, const LayerGate *lg, const LinTerm *lin, int sms, cudaStream_t s) {
+    (void)sms;
+    if (n_progs <= 0 || n_ctas == 0) return cudaSuccess;
+    // transposes and pending sums
+    constexpr int smem = ((int)(2 * sizeof(float)) << kTileQubits) + 6 * kTileThreads * 4;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_tile_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    k_tile_batch<<<n_ctas, kTileThreads, smem, s>>>(progs, first, n_progs, ops, lg, lin);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_tile_entries(const TileEntries &e, int nentries, int npats, TileEntries *dst, cudaStream_t s) {
-    if (nentries <= 0 && npats <= 0) return cudaSuccess;
-    k_tile_entries<<<1, 256, 0, s>>>(e, nentries, npats, dst);
-    return cudaGetLastError();
+cudaError_t launch_tile(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s) {
+    // 32-bit element offsets inside a tile reach 2^32 amplitudes
+    if (p.n <= 32) return launch_tile_t<uint32_t>(psi, p, cbits, s);
+    return launch_tile_t<uint64_t>(psi, p, cbits, s);
 }
 
 }  // namespace qk

@@ -75,7 +75,6 @@ struct qk_ctx {
 
     std::vector<qk::FusedOp> pending;   // fused-mode queue (physical qubits)
     qk::TilePlanner *planner = nullptr;
-    qk::TileEntries *d_tile_entries = nullptr;  // a tile pass's phase entries and patterns
 
     uint64_t launches = 0, passes_x1000 = 0;
     double alg_bytes = 0.0;
@@ -420,7 +419,6 @@ int ctx_sms(qk_ctx *c) { return c->sms; }
 int ctx_tile_qubits(qk_ctx *c) { return c->opt.tile_qubits; }
 cudaStream_t ctx_stream(qk_ctx *c) { return c->stream; }
 const uint8_t *ctx_cbits(qk_ctx *c) { return c->d_cbits; }
-TileEntries *ctx_tile_entries(qk_ctx *c) { return c->d_tile_entries; }
 qk_status ctx_run_plain(qk_ctx *c, const FusedOp &op) { return run_op_plain(c, op); }
 qk_status ctx_fail(qk_ctx *c, qk_status s, const char *msg) { return fail(c, s, "%s", msg); }
 void ctx_launch_begin(qk_ctx *c, int cls, double bytes, void **token) {
@@ -486,7 +484,6 @@ qk_status qk_create(qk_ctx **out, qk_precision precision, void *cuda_stream, con
         dalloc(c, (void **)&c->d_err, sizeof(int)) != cudaSuccess ||
         dalloc(c, (void **)&c->d_counter, sizeof(unsigned)) != cudaSuccess ||
         cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
-        dalloc(c, (void **)&c->d_tile_entries, sizeof(qk::TileEntries)) != cudaSuccess ||
         cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream) != cudaSuccess) {
         cudaGetLastError();
         qk_destroy(c);
@@ -511,7 +508,6 @@ qk_status qk_destroy(qk_ctx *c) {
     }
     dfree(c, c->d_err);
     dfree(c, c->d_counter);
-    dfree(c, c->d_tile_entries);
     dfree(c, c->d_swap_mat);
     dfree(c, c->d_state);
     dfree(c, c->d_scratch);

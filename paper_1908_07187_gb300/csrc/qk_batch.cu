@@ -11,20 +11,30 @@
 // Semantics match the per-gate engine op for op: measurement is one qubit at a
 // time in list order, P0 summed in FP64 over the (renormalised) state, outcome
 // 1 iff u >= P0, collapse and renormalise; cbits start at 0.
+//
+// Circuits of 14..24 qubits (unitary gates with at most one control) keep their
+// states in HBM: each is planned into fused tile passes on the host (in
+// parallel over the host's cores), and pass k of every such circuit runs in one
+// batched tile launch (k_tile_batch), so a batch of thousands of circuits costs
+// one launch per pass index rather than one per circuit pass.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "qk.h"
 #include "qk_host.h"
 #include "qk_kernels.cuh"
+#include "qk_plan.h"
 
 namespace qk {
 namespace {
@@ -32,6 +42,7 @@ namespace {
 constexpr int kBThreads = 256;
 constexpr int kBMaxQubits = 13;
 constexpr int kBMaxCbits = 64;
+constexpr int kBMaxLargeQubits = 24;
 constexpr int kOpChunk = kBThreads * 16 / 64;   // ops staged per chunk: one 16-byte word per thread
 
 enum BOpKind : uint8_t { B_U2 = 0, B_PHASE = 1, B_MULMOD = 2, B_MEASURE = 3 };
@@ -275,6 +286,12 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BCirc *__restrict__ c
         for (uint32_t i = tid; i < dim; i += kBThreads) states[c.state_off + i] = A[i];
 }
 
+// |0...0> for each listed state of the large-circuit pool (the pool is zeroed first)
+__global__ void k_set_basis0(float2 *pool, const uint64_t *offs, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) pool[offs[i]] = make_float2(1.f, 0.f);
+}
+
 }  // namespace
 }  // namespace qk
 
@@ -305,6 +322,33 @@ struct qk_batch {
     cudaEvent_t done = nullptr;
     bool store_state = true;
     std::string err;
+    // circuits of 14..24 qubits: gate lists for the tile planner, states in HBM
+    struct Large {
+        int circ;                      // index in circs
+        int n;
+        std::vector<qk::FusedOp> ops;  // physical qubit = qubit (no relabelling)
+        uint64_t state_off = 0;        // in the large-state pool, amplitudes
+        int npasses = 0;
+    };
+    std::vector<Large> large;
+    std::vector<int> large_of;         // circuit index -> index in large (-1: small)
+    uint64_t large_amps = 0;
+    float2 *d_lstates = nullptr;
+    size_t cap_lstates = 0;
+    qk::TileProg *d_lprogs = nullptr;
+    size_t cap_lprogs = 0;
+    uint32_t *d_lfirst = nullptr;
+    size_t cap_lfirst = 0;
+    uint64_t *d_loffs = nullptr;
+    size_t cap_loffs = 0;
+    qk::TileOp *d_lops = nullptr;
+    size_t cap_lops = 0;
+    qk::LayerGate *d_llg = nullptr;
+    size_t cap_llg = 0;
+    qk::LinTerm *d_llin = nullptr;
+    size_t cap_llin = 0;
+    double plan_ms = 0.0;              // host planning time of the last run
+    int large_launches = 0;            // batched tile launches of the last run
 };
 
 namespace {
@@ -359,6 +403,141 @@ bool distinct(const int *q, int k, int n) {
     return true;
 }
 
+// The circuits above 13 qubits: plan each into tile passes (host threads), pack
+// the pass programs into device pools ordered by pass index, set the states to
+// |0...0> and launch pass k of every circuit that has one in one batched launch.
+qk_status run_large(qk_batch *b) {
+    const auto t0 = std::chrono::steady_clock::now();
+    struct Plan {
+        std::vector<qk::TileProg> progs;
+        std::vector<qk::TileOp> ops;
+        std::vector<qk::LayerGate> lg;
+        std::vector<qk::LinTerm> lin;
+        qk_status st = QK_OK;
+        std::string err;
+    };
+    const int nl = (int)b->large.size();
+    std::vector<Plan> plans(nl);
+    const int nth = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::atomic<int> next(0);
+    auto worker = [&]() {
+        qk::TilePlanner *pl = qk::make_planner();
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= nl) break;
+            const auto &L = b->large[i];
+            Plan &out = plans[i];
+            const qk::PassSink sink = [&](qk::TileParams &P) -> qk_status {
+                if (P.n_conds > 0) {   // unreachable: large circuits take no classical conditions
+                    out.err = "batch: classical conditions are not batched above 13 qubits";
+                    return QK_EINVAL;
+                }
+                qk::TileProg h{};
+                static_cast<qk::TileHead &>(h) = P;
+                h.pf_dist = 0;
+                h.op0 = (uint32_t)out.ops.size();
+                h.lg0 = (uint32_t)out.lg.size();
+                h.lin0 = (uint32_t)out.lin.size();
+                out.ops.insert(out.ops.end(), P.ops, P.ops + P.nops);
+                out.lg.insert(out.lg.end(), P.lg, P.lg + P.nlg);
+                out.lin.insert(out.lin.end(), P.lin, P.lin + P.nlin);
+                out.progs.push_back(h);
+                return QK_OK;
+            };
+            const char *err = "";
+            out.st = qk::plan_passes(pl, L.n, L.ops, sink, &err);
+            if (out.st != QK_OK && out.err.empty()) out.err = err;
+        }
+        qk::free_planner(pl);
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t) th.emplace_back(worker);
+    for (auto &t : th) t.join();
+    size_t nops = 0, nlg = 0, nlin = 0, nprog = 0;
+    int maxp = 0;
+    std::vector<size_t> op_base(nl), lg_base(nl), lin_base(nl);
+    for (int i = 0; i < nl; ++i) {
+        if (plans[i].st != QK_OK) return bfail(b, plans[i].st, "batch: circuit %d: %s", b->large[i].circ, plans[i].err.c_str());
+        op_base[i] = nops;
+        lg_base[i] = nlg;
+        lin_base[i] = nlin;
+        nops += plans[i].ops.size();
+        nlg += plans[i].lg.size();
+        nlin += plans[i].lin.size();
+        nprog += plans[i].progs.size();
+        b->large[i].npasses = (int)plans[i].progs.size();
+        maxp = std::max(maxp, b->large[i].npasses);
+    }
+    qk_status s;
+    if ((s = grow(b, &b->d_lstates, &b->cap_lstates, std::max<uint64_t>(1, b->large_amps))) != QK_OK) return s;
+    if ((s = grow(b, &b->d_lprogs, &b->cap_lprogs, std::max<size_t>(1, nprog))) != QK_OK) return s;
+    if ((s = grow(b, &b->d_lfirst, &b->cap_lfirst, nprog + (size_t)maxp + 1)) != QK_OK) return s;
+    if ((s = grow(b, &b->d_loffs, &b->cap_loffs, (size_t)nl)) != QK_OK) return s;
+    if ((s = grow(b, &b->d_lops, &b->cap_lops, std::max<size_t>(1, nops))) != QK_OK) return s;
+    if ((s = grow(b, &b->d_llg, &b->cap_llg, std::max<size_t>(1, nlg))) != QK_OK) return s;
+    if ((s = grow(b, &b->d_llin, &b->cap_llin, std::max<size_t>(1, nlin))) != QK_OK) return s;
+    // programs ordered by pass index; first[] splits each launch's grid
+    std::vector<qk::TileProg> progs;
+    progs.reserve(nprog);
+    std::vector<uint32_t> first;
+    std::vector<std::pair<size_t, size_t>> launch;   // (first program, first[] index)
+    std::vector<uint32_t> ctas;
+    for (int k = 0; k < maxp; ++k) {
+        launch.push_back({progs.size(), first.size()});
+        uint32_t acc = 0;
+        for (int i = 0; i < nl; ++i) {
+            if (k >= (int)plans[i].progs.size()) continue;
+            qk::TileProg h = plans[i].progs[k];
+            h.op0 += (uint32_t)op_base[i];
+            h.lg0 += (uint32_t)lg_base[i];
+            h.lin0 += (uint32_t)lin_base[i];
+            h.psi = b->d_lstates + b->large[i].state_off;
+            progs.push_back(h);
+            first.push_back(acc);
+            acc += (uint32_t)h.n_tiles;
+        }
+        first.push_back(acc);
+        ctas.push_back(acc);
+    }
+    std::vector<qk::TileOp> ops;
+    std::vector<qk::LayerGate> lg;
+    std::vector<qk::LinTerm> lin;
+    ops.reserve(nops);
+    lg.reserve(nlg);
+    lin.reserve(nlin);
+    std::vector<uint64_t> offs(nl);
+    for (int i = 0; i < nl; ++i) {
+        ops.insert(ops.end(), plans[i].ops.begin(), plans[i].ops.end());
+        lg.insert(lg.end(), plans[i].lg.begin(), plans[i].lg.end());
+        lin.insert(lin.end(), plans[i].lin.begin(), plans[i].lin.end());
+        offs[i] = b->large[i].state_off;
+    }
+    b->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        return bytes == 0 || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, b->stream) == cudaSuccess;
+    };
+    if (!up(b->d_lprogs, progs.data(), sizeof(qk::TileProg) * progs.size()) ||
+        !up(b->d_lfirst, first.data(), sizeof(uint32_t) * first.size()) ||
+        !up(b->d_loffs, offs.data(), sizeof(uint64_t) * offs.size()) ||
+        !up(b->d_lops, ops.data(), sizeof(qk::TileOp) * ops.size()) ||
+        !up(b->d_llg, lg.data(), sizeof(qk::LayerGate) * lg.size()) ||
+        !up(b->d_llin, lin.data(), sizeof(qk::LinTerm) * lin.size()))
+        return bfail(b, QK_ECUDA, "batch: program upload failed");
+    if (cudaMemsetAsync(b->d_lstates, 0, sizeof(float2) * b->large_amps, b->stream) != cudaSuccess)
+        return bfail(b, QK_ECUDA, "batch: state reset failed");
+    qk::k_set_basis0<<<(nl + 255) / 256, 256, 0, b->stream>>>(b->d_lstates, b->d_loffs, nl);
+    if (cudaGetLastError() != cudaSuccess) return bfail(b, QK_ECUDA, "batch: state reset failed");
+    b->large_launches = 0;
+    for (int k = 0; k < maxp; ++k) {
+        const int np = (int)((k + 1 < maxp ? launch[k + 1].first : progs.size()) - launch[k].first);
+        const cudaError_t e = qk::launch_tile_batch(b->d_lprogs + launch[k].first, b->d_lfirst + launch[k].second, np,
+                                                    ctas[k], b->d_lops, b->d_llg, b->d_llin, b->sms, b->stream);
+        if (e != cudaSuccess) return bfail(b, QK_ECUDA, "batch: tile launch failed: %s", cudaGetErrorString(e));
+        ++b->large_launches;
+    }
+    return QK_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -399,6 +578,13 @@ qk_status qk_batch_destroy(qk_batch *b) {
     cudaFree(b->d_circs);
     cudaFree(b->d_states);
     cudaFree(b->d_cbits);
+    cudaFree(b->d_lstates);
+    cudaFree(b->d_lprogs);
+    cudaFree(b->d_lfirst);
+    cudaFree(b->d_loffs);
+    cudaFree(b->d_lops);
+    cudaFree(b->d_llg);
+    cudaFree(b->d_llin);
     if (b->h_stage) cudaFreeHost(b->h_stage);
     if (b->done) cudaEventDestroy(b->done);
     if (b->own_stream) cudaStreamDestroy(b->stream);
@@ -415,23 +601,39 @@ qk_status qk_batch_clear(qk_batch *b) {
     b->total_amps = 0;
     b->total_cb = 0;
     b->max_n = 0;
+    b->large.clear();
+    b->large_of.clear();
+    b->large_amps = 0;
     return QK_OK;
 }
 
 qk_status qk_batch_add_circuit(qk_batch *b, int n, int ncbits, int *index) {
     if (!b) return QK_EINVAL;
-    if (n < 1 || n > qk::kBMaxQubits) return bfail(b, QK_EINVAL, "batch: circuits take 1..%d qubits", qk::kBMaxQubits);
+    if (n < 1 || n > qk::kBMaxLargeQubits)
+        return bfail(b, QK_EINVAL, "batch: circuits take 1..%d qubits", qk::kBMaxLargeQubits);
     if (ncbits < 0 || ncbits > qk::kBMaxCbits) return bfail(b, QK_EINVAL, "batch: at most %d cbits", qk::kBMaxCbits);
     qk::BCirc c{};
     c.op_begin = c.op_end = (uint32_t)b->ops.size();
     c.n = (uint32_t)n;
     c.ncb = (uint32_t)ncbits;
     c.cb_off = b->total_cb;
-    c.state_off = b->total_amps;
     b->total_cb += (uint32_t)ncbits;
-    b->total_amps += 1ull << n;
-    b->max_n = std::max(b->max_n, n);
     if (index) *index = (int)b->circs.size();
+    if (n > qk::kBMaxQubits) {
+        qk_batch::Large L;
+        L.circ = (int)b->circs.size();
+        L.n = n;
+        L.state_off = b->large_amps;
+        b->large_amps += 1ull << n;
+        c.flags |= 2u;    // a large circuit: state in the large pool, no BOps
+        b->large_of.push_back((int)b->large.size());
+        b->large.push_back(std::move(L));
+    } else {
+        c.state_off = b->total_amps;
+        b->total_amps += 1ull << n;
+        b->max_n = std::max(b->max_n, n);
+        b->large_of.push_back(-1);
+    }
     b->circs.push_back(c);
     return QK_OK;
 }
@@ -453,10 +655,36 @@ qk_status qk_batch_apply_gate(qk_batch *b, int gate_id, const int *targets, int 
         if (controls[k] == targets[0]) return bfail(b, QK_EINVAL, "batch: control equals target");
         cmask |= 1u << controls[k];
     }
+    const int q = targets[0];
+    if (c->flags & 2u) {  // large circuit: ops for the tile planner
+        if (ncc != 0 || nc > 1)
+            return bfail(b, QK_EINVAL, "batch: circuits above %d qubits take gates with at most one control and no "
+                                       "classical condition", qk::kBMaxQubits);
+        auto &L = b->large[b->large_of.back()];
+        if (m[1] == 0.0 && m[2] == 0.0) {  // diagonal: one phase op per entry that is not 1
+            for (int e = 0; e < 2; ++e) {
+                const qk::cd f = e ? m[3] : m[0];
+                if (f == 1.0) continue;
+                qk::FusedOp o;
+                o.kind = qk::FusedOp::PHASE;
+                o.mask = (uint64_t)cmask | (1ull << q);
+                o.val = (uint64_t)cmask | (e ? (1ull << q) : 0ull);
+                o.f = f;
+                L.ops.push_back(o);
+            }
+        } else {
+            qk::FusedOp o;
+            o.kind = qk::FusedOp::U2;
+            o.q = q;
+            o.cmask = cmask;
+            for (int e = 0; e < 4; ++e) o.m[e] = m[e];
+            L.ops.push_back(o);
+        }
+        return QK_OK;
+    }
     qk::BOp op;
     std::memset(&op, 0, sizeof op);
     if (!fill_cond(op, *c, cond_cbits, ncc)) return bfail(b, QK_EINVAL, "batch: bad classical condition");
-    const int q = targets[0];
     if (m[1] == 0.0 && m[2] == 0.0) {  // diagonal: one phase op per entry that is not 1
         for (int e = 0; e < 2; ++e) {
             const qk::cd f = e ? m[3] : m[0];
@@ -506,6 +734,7 @@ qk_status qk_batch_apply_mulmod(qk_batch *b, const int *targets, int w, const in
     qk::BCirc *c;
     if (!cur_circuit(b, &c)) return bfail(b, QK_ESTATE, "batch: add a circuit first");
     const int n = (int)c->n;
+    if (c->flags & 2u) return bfail(b, QK_EINVAL, "batch: circuits above %d qubits take unitary gates only", qk::kBMaxQubits);
     if (w < 1 || w > 16 || !distinct(targets, w, n) || nc < 0 || (nc > 0 && !distinct(controls, nc, n)))
         return bfail(b, QK_EINVAL, "batch: bad mul-mod register or controls");
     if (N < 2 || N > (1ull << w) || cc >= N) return bfail(b, QK_EINVAL, "batch: need 2 <= N <= 2^w and c < N");
@@ -534,6 +763,7 @@ qk_status qk_batch_measure(qk_batch *b, const int *qubits, int nq, const double 
     if (!b) return QK_EINVAL;
     qk::BCirc *c;
     if (!cur_circuit(b, &c)) return bfail(b, QK_ESTATE, "batch: add a circuit first");
+    if (c->flags & 2u) return bfail(b, QK_EINVAL, "batch: circuits above %d qubits take unitary gates only", qk::kBMaxQubits);
     if (nq < 1 || !distinct(qubits, nq, (int)c->n) || !uniforms) return bfail(b, QK_EINVAL, "batch: bad qubit list");
     for (int k = 0; k < nq; ++k) {
         if (!(uniforms[k] >= 0.0 && uniforms[k] < 1.0)) return bfail(b, QK_EINVAL, "batch: uniform not in [0, 1)");
@@ -556,12 +786,21 @@ qk_status qk_batch_run(qk_batch *b, int store_states) {
     b->store_state = store_states != 0;
     qk_status s;
     if ((s = grow(b, &b->d_ops, &b->cap_ops, std::max<size_t>(1, b->ops.size()))) != QK_OK) return s;
-    if ((s = grow(b, &b->d_circs, &b->cap_circs, b->circs.size())) != QK_OK) return s;
+    if ((s = grow(b, &b->d_circs, &b->cap_circs, std::max<size_t>(1, b->circs.size()))) != QK_OK) return s;
     if (b->store_state && (s = grow(b, &b->d_states, &b->cap_states, b->total_amps)) != QK_OK) return s;
     if ((s = grow(b, &b->d_cbits, &b->cap_cbits, std::max<size_t>(1, b->total_cb))) != QK_OK) return s;
+    // circuits of at most 13 qubits, sorted by size: one launch per qubit count (and
+    // per need of the second state buffer, which only mul-mod gathers use), each
+    // sized to its shared memory (small circuits then share an SM)
+    std::vector<qk::BCirc> sorted;
+    for (const auto &c : b->circs)
+        if (!(c.flags & 2u)) sorted.push_back(c);
+    std::stable_sort(sorted.begin(), sorted.end(), [](const qk::BCirc &x, const qk::BCirc &y) {
+        return x.n != y.n ? x.n < y.n : (x.flags & 1u) < (y.flags & 1u);
+    });
     // stage the program in pinned memory so that the copies are truly asynchronous
-    const size_t ob = sizeof(qk::BOp) * b->ops.size(), cb = sizeof(qk::BCirc) * b->circs.size();
-    if (ob + cb > b->cap_stage) {
+    const size_t ob = sizeof(qk::BOp) * b->ops.size(), cb = sizeof(qk::BCirc) * sorted.size();
+    if (ob + cb > 0 && ob + cb > b->cap_stage) {
         if (b->h_stage) cudaFreeHost(b->h_stage);
         b->h_stage = nullptr;
         b->cap_stage = 0;
@@ -571,20 +810,15 @@ qk_status qk_batch_run(qk_batch *b, int store_states) {
         }
         b->cap_stage = (ob + cb) * 2;
     }
-    // circuits sorted by size: one launch per qubit count (and per need of the
-    // second state buffer, which only mul-mod gathers use), each sized to its
-    // shared memory (small circuits then share an SM)
-    std::vector<qk::BCirc> sorted(b->circs);
-    std::stable_sort(sorted.begin(), sorted.end(), [](const qk::BCirc &x, const qk::BCirc &y) {
-        return x.n != y.n ? x.n < y.n : (x.flags & 1u) < (y.flags & 1u);
-    });
-    std::memcpy(b->h_stage, b->ops.data(), ob);
-    std::memcpy((char *)b->h_stage + ob, sorted.data(), cb);
-    if (cudaMemcpyAsync(b->d_ops, b->h_stage, ob, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-        cudaMemcpyAsync(b->d_circs, (char *)b->h_stage + ob, cb, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
-        return bfail(b, QK_ECUDA, "batch: upload failed");
+    if (ob + cb > 0) {
+        std::memcpy(b->h_stage, b->ops.data(), ob);
+        std::memcpy((char *)b->h_stage + ob, sorted.data(), cb);
+        if (cudaMemcpyAsync(b->d_ops, b->h_stage, ob, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+            cudaMemcpyAsync(b->d_circs, (char *)b->h_stage + ob, cb, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+            return bfail(b, QK_ECUDA, "batch: upload failed");
+    }
     const size_t max_smem = sizeof(float2) * 2 * ((size_t)1 << b->max_n);
-    if (max_smem > 48 * 1024 &&
+    if (!sorted.empty() && max_smem > 48 * 1024 &&
         cudaFuncSetAttribute(qk::k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem) != cudaSuccess)
         return bfail(b, QK_ECUDA, "batch: shared memory attribute failed");
     for (size_t i = 0; i < sorted.size();) {
@@ -597,7 +831,18 @@ qk_status qk_batch_run(qk_batch *b, int store_states) {
         if (cudaGetLastError() != cudaSuccess) return bfail(b, QK_ECUDA, "batch: launch failed");
         i = j;
     }
+    if (!b->large.empty()) {
+        const qk_status ls = run_large(b);
+        if (ls != QK_OK) return ls;
+    }
     if (cudaEventRecord(b->done, b->stream) != cudaSuccess) return bfail(b, QK_ECUDA, "batch: event record failed");
+    return QK_OK;
+}
+
+qk_status qk_batch_stats(const qk_batch *b, double *plan_ms, int *tile_launches) {
+    if (!b) return QK_EINVAL;
+    if (plan_ms) *plan_ms = b->plan_ms;
+    if (tile_launches) *tile_launches = b->large_launches;
     return QK_OK;
 }
 
@@ -617,12 +862,14 @@ qk_status qk_batch_read(qk_batch *b, int circuit, uint8_t *cbits, int ncb, void 
     if (circuit < 0 || circuit >= (int)b->circs.size()) return bfail(b, QK_EINVAL, "batch: bad circuit index");
     const qk::BCirc &c = b->circs[circuit];
     if (ncb < 0 || ncb > (int)c.ncb || (ncb > 0 && !cbits)) return bfail(b, QK_EINVAL, "batch: bad cbit count");
-    if (state && (!b->store_state || bytes != sizeof(float2) << c.n))
+    const bool large = (c.flags & 2u) != 0;
+    if (state && ((!large && !b->store_state) || bytes != sizeof(float2) << c.n))
         return bfail(b, QK_EINVAL, "batch: state not stored or wrong size (%zu bytes expected)", sizeof(float2) << c.n);
     if (cudaEventSynchronize(b->done) != cudaSuccess) return bfail(b, QK_ECUDA, "batch: event wait failed");
     if (ncb > 0 && cudaMemcpy(cbits, b->d_cbits + c.cb_off, ncb, cudaMemcpyDeviceToHost) != cudaSuccess)
         return bfail(b, QK_ECUDA, "batch: cbit copy failed");
-    if (state && cudaMemcpy(state, b->d_states + c.state_off, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+    const float2 *src = large ? b->d_lstates + b->large[b->large_of[circuit]].state_off : b->d_states + c.state_off;
+    if (state && cudaMemcpy(state, src, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
         return bfail(b, QK_ECUDA, "batch: state copy failed");
     return QK_OK;
 }

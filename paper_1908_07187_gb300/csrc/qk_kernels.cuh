@@ -253,69 +253,38 @@ constexpr int kTileQubits = 13;
 constexpr int kTileContig = 5;
 constexpr int kTileThreads = 256;
 constexpr int kTileMaxOps = 192;
-constexpr int kTileMaxEntries = 512;
-constexpr int kTileMaxPats = 64;
 constexpr int kTileMaxLin = 512;
 // runs of consecutive fixed qubits: S holds 0..4 and eight more bits, which
 // split the rest into at most nine runs
 constexpr int kTileMaxRuns = 12;
 constexpr int kTileMaxMats = 160;
 constexpr int kTileMaxConds = 4;
-constexpr int kTileMaxPhOps = 24;   // TOP_PHASES ops per pass (their sums live in shared memory)
 enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
-// TOP_PHASES: a group of thread- or tile-dependent diagonal terms that all add to
-// one pending phase sum (register bit k, or the thread constant when k == 5), as
-// patterns [first, first + count): each pattern is the terms sharing one
-// thread-bit condition; its fixed-bit-conditioned terms are entries in global
-// memory, summed by one thread per pattern (the condition is uniform over a
-// tile).  The sums do not depend on the amplitudes, so every TOP_PHASES op of a
-// pass is summed when a tile starts and kept in shared memory (slot count2) until
-// the op runs.  Diagonal terms that are the same for every amplitude pair of a
-// qubit (no thread or fixed-bit condition) never reach the device: the planner
-// folds them into the next layer gate's coefficients or into the final flush.
 // TOP_U2L: a layer of uncontrolled 2x2 gates on distinct register bits (k is
 // the bit mask), in pivot form; their coefficients are lg[first...] in bit order.
-// TOP_PAIR: factor on the amplitudes whose register bits k and l are both 1
-// (code k | l << 3), under the op's thread / fixed-bit conditions.
-// TOP_PHASEL: the common form of such a group, a sum of linear terms lin[first,
-// first + count) evaluated in place (see LinTerm).  For TOP_PHASES and TOP_PHASEL,
-// rval = 1 says that bit k's qubit is stored flipped, so the sum lands on k = 0.
-// TOP_PAIR: rval holds the values of the pair's two bits that the factor needs.
+// TOP_PHASEL: a group of thread- or tile-dependent diagonal terms that all add to
+// one pending phase sum (register bit k, or the thread constant when k == 5):
+// lin[first, first + count), evaluated in place (see LinTerm); rval = 1 says that
+// bit k's qubit is stored flipped, so the sum lands on k = 0.  Diagonal terms
+// that are the same for every amplitude pair of a qubit (no thread or fixed-bit
+// condition) never reach the device: the planner folds them into the next layer
+// gate's coefficients or into the final flush.
+// TOP_PAIR: factor on the amplitudes whose register bits k and l (code k | l <<
+// 3) have the values in rval (bit 0: k, bit 1: l), under the op's thread /
+// fixed-bit conditions.
 // TOP_PAIRNEG: an unconditional sign flip of the amplitudes whose register bits k
 // and l are both 1 (code k | l << 3): a CZ between two register bits.
 enum TileOpKind : uint8_t {
-    TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_PHASES = 3, TOP_U2L = 4, TOP_PAIR = 5, TOP_PHASEL = 6,
-    TOP_PAIRNEG = 7
+    TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_U2L = 4, TOP_PAIR = 5, TOP_PHASEL = 6, TOP_PAIRNEG = 7
 };
 
 // A diagonal term of a TOP_PHASEL group: adds turns where the thread bits match
-// (tbits & tmask) == tval and, unless fbit == 0xff, bit fbit of the tile index
-// (the fixed qubit P.fixed[fbit]) is 1.  Terms on a fixed qubit being 0 are
-// written as the unconditional term minus the conditional one.
+// (tbits & tmask) == tval and the tile index matches (tile & fmask) == fval (its
+// bit b is the fixed qubit fixed[b]).
 struct LinTerm {
     uint16_t tmask, tval;
-    uint8_t fbit, pad[3];
+    uint32_t fmask, fval;
     uint32_t turns;
-};
-
-// A diagonal term conditioned on fixed (non-tile) bits: adds turns when
-// (tile base & gmask) == gval.
-struct PhaseEntry {
-    uint64_t gmask, gval;
-    uint32_t turns, pad;
-};
-// The terms of one TOP_PHASES group that share a thread-bit condition.
-struct PhasePattern {
-    uint16_t tmask, tval;
-    uint16_t first, count;  // entries [first, first + count)
-    uint32_t turns;         // sum of the terms without a fixed-bit condition
-};
-// A pass's entries and patterns, copied to a device buffer by a one-block kernel
-// before the tile kernel runs (kernel parameters serve a warp well only at
-// uniform addresses; the tile kernel reads these at per-thread addresses).
-struct TileEntries {
-    PhaseEntry e[kTileMaxEntries];
-    PhasePattern p[kTileMaxPats];
 };
 
 // One gate of a TOP_U2L layer in pivot form.  The planner may keep a local
@@ -339,8 +308,8 @@ struct TileOp {
     uint8_t rmask, rval;   // condition on register bits (5-bit register index space)
     uint16_t tmask, tval;  // condition on thread bits: bits 0..4 lane, 5..7 warp
     uint16_t cond;         // index into TileParams::conds, 0xffff = unconditional
-    uint16_t count;        // TOP_PHASES: patterns [first, first + count); TOP_U2L: gates
-    uint16_t first;        //   from lg[first]
+    uint16_t count;        // TOP_U2L: gates from lg[first]; TOP_PHASEL: terms from lin[first]
+    uint16_t first;
     uint16_t count2;
     uint32_t hturns;       // TOP_U2: uniform pending turns of the target's qubit, added
                            // to the thread's pending sum before the op
@@ -355,7 +324,9 @@ struct TileOp {
     };
 };
 
-struct TileParams {
+// The scalar part of a tile-pass program (the arrays follow in TileParams, or
+// sit in device pools for a batched launch, see TileProg).
+struct TileHead {
     uint64_t n_tiles;
     int n;
     int nfix;
@@ -369,26 +340,37 @@ struct TileParams {
     int n_conds;
     Cond conds[kTileMaxConds];
     int nops;
-    int nentries;
-    int npats;
-    int nphops;                             // TOP_PHASES ops; op.count2 is the op's slot
-    uint16_t phop[kTileMaxPhOps][2];        // slot -> (first pattern, pattern count)
     // final flush: the uniform pending phase of each local qubit's |1> (turns), the
     // uniform constant phase (fin_turns[13]) and the pass's real scale
     uint32_t fin_turns[14];
     float fin_scale;
     int fin_flip;          // local qubits stored flipped at the end (bit b: local qubit b)
     uint32_t pf_dist;      // L2 prefetch of the tile this many CTAs ahead (0: none)
+    int nlg, nlin;         // entries of lg[] and lin[] in use
+};
+
+// A whole pass program, passed as kernel parameters for one state.
+struct TileParams : TileHead {
     TileOp ops[kTileMaxOps];
-    PhasePattern pats[kTileMaxPats];
     LayerGate lg[kTileMaxMats];
     LinTerm lin[kTileMaxLin];
 };
+
+// A pass program of one circuit in a batched launch: the header plus offsets
+// of its ops, layer gates and linear terms in device pools, and its state.
+struct TileProg : TileHead {
+    uint32_t op0, lg0, lin0, pad;
+    float2 *psi;
+};
 static_assert(sizeof(TileParams) <= 32764, "tile program must fit in the kernel parameter space");
 
-cudaError_t launch_tile(void *psi, const TileParams &p, const TileEntries *entries, const uint8_t *cbits,
-                        cudaStream_t s);
-cudaError_t launch_tile_entries(const TileEntries &e, int nentries, int npats, TileEntries *dst, cudaStream_t s);
+cudaError_t launch_tile(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s);
+// Pass k of many circuits in one launch: CTA b runs tile (b - first[c]) of
+// program c, where first[] (n_progs + 1 entries, ascending, first[0] = 0) splits
+// the grid; programs are in n-qubit order so that the 32-bit offset kernel serves
+// every circuit below 33 qubits.
+cudaError_t launch_tile_batch(const TileProg *progs, const uint32_t *first, int n_progs, uint32_t n_ctas,
+                              const TileOp *ops, const LayerGate *lg, const LinTerm *lin, int sms, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // launchers (kernels_basic.cu); prec: 0 = complex64, 1 = complex128

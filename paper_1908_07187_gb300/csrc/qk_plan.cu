@@ -197,15 +197,9 @@ int local_of_tbit(int arr, int t) {
 }
 }  // namespace
 
-qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> &ops) {
-    const int n = ctx_n(c);
-    if (n < kTileQubits || ctx_prec(c) != 0) {
-        for (const auto &op : ops) {
-            qk_status s = ctx_run_plain(c, op);
-            if (s != QK_OK) return s;
-        }
-        return QK_OK;
-    }
+qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &ops, const PassSink &sink,
+                      const char **err) {
+    *err = "";
     std::vector<POp> rem;
     rem.reserve(ops.size());
     for (const auto &op : ops) rem.push_back(classify(op));
@@ -262,8 +256,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             }
 
         static thread_local TileParams P;
-        static thread_local TileEntries E;
-        std::memset(&P, 0, offsetof(TileParams, ops));
+        std::memset(static_cast<TileHead *>(&P), 0, sizeof(TileHead));
         P.n = n;
         P.n_tiles = 1ull << (n - kTileQubits);
         int local_of[64];
@@ -284,7 +277,10 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             for (int b = 0; b < fb;) {
                 int e = b + 1;
                 while (e < fb && P.fixed[e] == P.fixed[e - 1] + 1) ++e;
-                if (P.nruns >= kTileMaxRuns) return ctx_fail(c, QK_EINVAL, "internal: too many fixed-qubit runs");
+                if (P.nruns >= kTileMaxRuns) {
+                    *err = "internal: too many fixed-qubit runs";
+                    return QK_EINVAL;
+                }
                 P.run_tlo[P.nruns] = (uint8_t)b;
                 P.run_len[P.nruns] = (uint8_t)(e - b);
                 P.run_plo[P.nruns] = (uint8_t)P.fixed[b];
@@ -381,7 +377,7 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
         // group runs of consecutive diagonal terms by the pending sum they feed
         {
             static thread_local TileOp out[2 * kTileMaxOps + 8];
-            int nout = 0, nent = 0, npat = 0, nph = 0, nlin = 0;
+            int nout = 0, nlin = 0;
             int fixed_index[64];   // physical qubit -> bit of the tile index
             for (int b = 0; b < 64; ++b) fixed_index[b] = -1;
             for (int b = 0; b < P.nfix; ++b) fixed_index[(int)P.fixed[b]] = b;
@@ -499,40 +495,37 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 }
                 for (int g = 0; g < 6 && !overflow; ++g) {
                     if (grp[g].empty()) continue;
-                    // split the group's terms: the same for every thread (kept by the
-                    // planner), linear (thread-bit condition and at most one fixed
-                    // qubit that must be 1: TOP_PHASEL), general (TOP_PHASES)
+                    // split the group's terms: the same for every thread and tile
+                    // (kept by the planner), and the rest, each a linear term with
+                    // its thread-bit and tile-index conditions (TOP_PHASEL)
                     uint32_t host_turns = 0;
                     std::vector<LinTerm> lins;
-                    std::vector<Term> general;
-                    auto add_lin = [&](uint16_t tm, uint16_t tv, uint8_t fb, uint32_t tu) {
-                        for (auto &l : lins)
-                            if (l.tmask == tm && l.tval == tv && l.fbit == fb) {
-                                l.turns += tu;
-                                return;
-                            }
-                        LinTerm l{};
-                        l.tmask = tm;
-                        l.tval = tv;
-                        l.fbit = fb;
-                        l.turns = tu;
-                        lins.push_back(l);
-                    };
                     for (const Term &t : grp[g]) {
-                        if (t.gmask == 0) {
-                            if (t.tmask == 0) host_turns += t.turns;
-                            else add_lin(t.tmask, t.tval, 0xff, t.turns);
-                        } else if (__builtin_popcountll(t.gmask) == 1) {
-                            const uint8_t fb = (uint8_t)fixed_index[__builtin_ctzll(t.gmask)];
-                            if (t.gval) {
-                                add_lin(t.tmask, t.tval, fb, t.turns);
-                            } else {  // on the fixed qubit being 0: unconditional minus on 1
-                                if (t.tmask == 0) host_turns += t.turns;
-                                else add_lin(t.tmask, t.tval, 0xff, t.turns);
-                                add_lin(t.tmask, t.tval, fb, 0u - t.turns);
+                        if (t.gmask == 0 && t.tmask == 0) {
+                            host_turns += t.turns;
+                            continue;
+                        }
+                        uint32_t fm = 0, fv = 0;   // the fixed-qubit condition on tile-index bits
+                        for (uint64_t mk = t.gmask; mk; mk &= mk - 1) {
+                            const int pb = __builtin_ctzll(mk), tb = fixed_index[pb];
+                            fm |= 1u << tb;
+                            if ((t.gval >> pb) & 1) fv |= 1u << tb;
+                        }
+                        bool merged = false;
+                        for (auto &l : lins)
+                            if (l.tmask == t.tmask && l.tval == t.tval && l.fmask == fm && l.fval == fv) {
+                                l.turns += t.turns;
+                                merged = true;
+                                break;
                             }
-                        } else {
-                            general.push_back(t);
+                        if (!merged) {
+                            LinTerm l{};
+                            l.tmask = t.tmask;
+                            l.tval = t.tval;
+                            l.fmask = fm;
+                            l.fval = fv;
+                            l.turns = t.turns;
+                            lins.push_back(l);
                         }
                     }
                     if (host_turns != 0) {
@@ -558,67 +551,15 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                             if (l.turns != 0) P.lin[nlin++] = l;
                         t.count = (uint16_t)(nlin - t.first);
                     }
-                    if (general.empty()) continue;
-                    // patterns: the general terms by thread-bit condition; within one,
-                    // terms with equal fixed-bit conditions merge
-                    std::sort(general.begin(), general.end(), [](const Term &a, const Term &b) {
-                        if (a.tmask != b.tmask) return a.tmask < b.tmask;
-                        if (a.tval != b.tval) return a.tval < b.tval;
-                        if (a.gmask != b.gmask) return a.gmask < b.gmask;
-                        return a.gval < b.gval;
-                    });
-                    const int pat0 = npat;
-                    for (size_t a = 0; a < general.size() && !overflow;) {
-                        size_t b = a;
-                        while (b < general.size() && general[b].tmask == general[a].tmask &&
-                               general[b].tval == general[a].tval)
-                            ++b;
-                        PhasePattern pt{};
-                        pt.tmask = general[a].tmask;
-                        pt.tval = general[a].tval;
-                        pt.first = (uint16_t)nent;
-                        for (size_t x = a; x < b;) {
-                            size_t y = x;
-                            uint32_t tu = 0;
-                            while (y < b && general[y].gmask == general[x].gmask && general[y].gval == general[x].gval)
-                                tu += general[y++].turns;
-                            if (tu != 0) {
-                                if (nent >= kTileMaxEntries) { overflow = true; break; }
-                                PhaseEntry &e = E.e[nent++];
-                                e.gmask = general[x].gmask;
-                                e.gval = general[x].gval;
-                                e.turns = tu;
-                                e.pad = 0;
-                            }
-                            x = y;
-                        }
-                        pt.count = (uint16_t)(nent - pt.first);
-                        if (!overflow && pt.count) {
-                            if (npat >= kTileMaxPats) { overflow = true; break; }
-                            E.p[npat] = pt;
-                            P.pats[npat++] = pt;
-                        }
-                        a = b;
-                    }
-                    if (overflow || npat == pat0) continue;
-                    if (nout >= 2 * kTileMaxOps || nph >= kTileMaxPhOps) { overflow = true; break; }
-                    TileOp &t = out[nout++];
-                    std::memset(&t, 0, sizeof t);
-                    t.kind = TOP_PHASES;
-                    t.k = (uint8_t)g;
-                    t.cond = 0xffff;
-                    t.first = (uint16_t)pat0;
-                    t.count = (uint16_t)(npat - pat0);
-                    t.count2 = (uint16_t)nph;
-                    P.phop[nph][0] = (uint16_t)pat0;
-                    P.phop[nph][1] = (uint16_t)(npat - pat0);
-                    ++nph;
                 }
                 i = j;
             }
             if (overflow || nout > kTileMaxOps) {
                 // too large for one launch: plan this pass again with fewer gates
-                if (max_u2 <= 1 && max_ph <= 1) return ctx_fail(c, QK_EINVAL, "internal: tile program overflow");
+                if (max_u2 <= 1 && max_ph <= 1) {
+                    *err = "internal: tile program overflow";
+                    return QK_EINVAL;
+                }
                 max_u2 = std::max(1, max_u2 / 2);
                 max_ph = std::max(1, max_ph / 2);
                 continue;
@@ -661,7 +602,10 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 i = j;
             }
             if (overflow) {
-                if (max_u2 <= 1 && max_ph <= 1) return ctx_fail(c, QK_EINVAL, "internal: tile program overflow");
+                if (max_u2 <= 1 && max_ph <= 1) {
+                    *err = "internal: tile program overflow";
+                    return QK_EINVAL;
+                }
                 max_u2 = std::max(1, max_u2 / 2);
                 max_ph = std::max(1, max_ph / 2);
                 continue;
@@ -730,13 +674,6 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                                 P.lin[e].tval ^= (uint16_t)(P.lin[e].tmask & tflip);
                             o.rval = (uint8_t)(o.k < 5 ? (rflip >> o.k) & 1 : 0);
                             break;
-                        case TOP_PHASES:
-                            for (int q = o.first; q < o.first + o.count; ++q) {
-                                P.pats[q].tval ^= (uint16_t)(P.pats[q].tmask & tflip);
-                                E.p[q].tval = P.pats[q].tval;
-                            }
-                            o.rval = (uint8_t)(o.k < 5 ? (rflip >> o.k) & 1 : 0);
-                            break;
                         case TOP_PHASE:
                             o.rval ^= (uint8_t)(o.rmask & rflip);
                             o.tval ^= (uint16_t)(o.tmask & tflip);
@@ -771,9 +708,8 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
                 for (int q = 0; q < kTileQubits; ++q) P.fin_flip |= st.flip[q] << q;
             }
             nops = nfin;
-            P.nentries = nent;
-            P.npats = npat;
-            P.nphops = nph;
+            P.nlg = nmat;
+            P.nlin = nlin;
         }
         P.nops = nops;
         P.store_arr = cur;
@@ -782,11 +718,30 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             for (int i = 0; i < nops; ++i) cnt_k[P.ops[i].kind]++;
             std::fprintf(stderr,
                          "[qk plan] pass S=%#llx gates=%d (u2 %d, phase %d) ops=%d u2=%d layers=%d phase_direct=%d "
-                         "phase_groups=%d entries=%d pairs=%d xpose=%d store_arr=%d\n",
+                         "phase_groups=%d terms=%d pairs=%d pair_signs=%d xpose=%d store_arr=%d\n",
                          (unsigned long long)S, m, n_u2, n_ph, nops, cnt_k[TOP_U2], cnt_k[TOP_U2L], cnt_k[TOP_PHASE],
-                         cnt_k[TOP_PHASES], P.nentries, cnt_k[TOP_PAIR], cnt_k[TOP_XPOSE], cur);
+                         cnt_k[TOP_PHASEL], P.nlin, cnt_k[TOP_PAIR], cnt_k[TOP_PAIRNEG], cnt_k[TOP_XPOSE], cur);
         }
 
+        const qk_status st = sink(P);
+        if (st != QK_OK) return st;
+        rem.swap(left);
+        max_u2 = 100;
+        max_ph = 300;
+    }
+    return QK_OK;
+}
+
+qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> &ops) {
+    const int n = ctx_n(c);
+    if (n < kTileQubits || ctx_prec(c) != 0) {
+        for (const auto &op : ops) {
+            qk_status s = ctx_run_plain(c, op);
+            if (s != QK_OK) return s;
+        }
+        return QK_OK;
+    }
+    const PassSink launch = [&](TileParams &P) -> qk_status {
         void *tok = nullptr;
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         if (planner->log) {  // trace mode: time this pass on its own (synchronous)
@@ -794,15 +749,9 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             cudaEventCreate(&ev1);
             cudaEventRecord(ev0, ctx_stream(c));
         }
-        if (P.nphops > 0) {
-            ctx_launch_begin(c, 6, 2.0 * (sizeof(PhaseEntry) * P.nentries + sizeof(PhasePattern) * P.npats), &tok);
-            cudaError_t e = launch_tile_entries(E, P.nentries, P.npats, ctx_tile_entries(c), ctx_stream(c));
-            ctx_launch_end(tok);
-            if (e != cudaSuccess) return ctx_fail(c, QK_ECUDA, cudaGetErrorString(e));
-        }
         P.pf_dist = (uint32_t)(2 * ctx_sms(c));   // one wave of resident CTAs ahead
         ctx_launch_begin(c, 0, 2.0 * 8.0 * (double)(1ull << n), &tok);
-        cudaError_t e = launch_tile(ctx_state(c), P, ctx_tile_entries(c), ctx_cbits(c), ctx_stream(c));
+        cudaError_t e = launch_tile(ctx_state(c), P, ctx_cbits(c), ctx_stream(c));
         ctx_launch_end(tok);
         if (e != cudaSuccess) return ctx_fail(c, QK_ECUDA, cudaGetErrorString(e));
         if (planner->log) {
@@ -814,11 +763,12 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             cudaEventDestroy(ev0);
             cudaEventDestroy(ev1);
         }
-        rem.swap(left);
-        max_u2 = 100;
-        max_ph = 300;
-    }
-    return QK_OK;
+        return QK_OK;
+    };
+    const char *err = "";
+    const qk_status st = plan_passes(planner, n, ops, launch, &err);
+    if (st != QK_OK && err[0]) return ctx_fail(c, st, err);
+    return st;
 }
 
 }  // namespace qk

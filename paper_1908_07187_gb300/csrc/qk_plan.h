@@ -3,6 +3,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -27,6 +28,13 @@ struct FusedOp {
 struct TilePlanner;
 TilePlanner *make_planner();
 void free_planner(TilePlanner *p);
+// Plan an n-qubit (n >= 13) complex64 op list into tile passes; each pass's
+// program goes to sink in order (it may modify the program, e.g. set pf_dist).
+// On a planner error *err names it.
+using PassSink = std::function<qk_status(TileParams &)>;
+qk_status plan_passes(TilePlanner *p, int n, const std::vector<FusedOp> &ops, const PassSink &sink, const char **err);
+// plan_passes with each pass launched on the context's stream (n < 13 or
+// complex128: one plain launch per op)
 qk_status run_fused(TilePlanner *p, qk_ctx *c, const std::vector<FusedOp> &ops);
 
 // context hooks implemented in qk_api.cu
@@ -37,7 +45,6 @@ int ctx_sms(qk_ctx *c);
 int ctx_tile_qubits(qk_ctx *c);
 cudaStream_t ctx_stream(qk_ctx *c);
 const uint8_t *ctx_cbits(qk_ctx *c);
-TileEntries *ctx_tile_entries(qk_ctx *c);   // device copy of a pass's phase entries and patterns
 qk_status ctx_run_plain(qk_ctx *c, const FusedOp &op);
 qk_status ctx_fail(qk_ctx *c, qk_status s, const char *msg);
 void ctx_launch_begin(qk_ctx *c, int cls, double bytes, void **token);

@@ -126,6 +126,7 @@ _SIGS = {
     "qk_batch_read": ([_P, ctypes.c_int, _U8P, ctypes.c_int, _P, ctypes.c_size_t], ctypes.c_int),
     "qk_batch_read_all_cbits": ([_P, _U8P, ctypes.c_size_t], ctypes.c_int),
     "qk_batch_num_circuits": ([_P], ctypes.c_int),
+    "qk_batch_stats": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "qk_batch_last_error": ([_P], ctypes.c_char_p),
     "qk_last_error": ([_P], ctypes.c_char_p),
     "qk_status_str": ([ctypes.c_int], ctypes.c_char_p),
@@ -376,9 +377,12 @@ class Graph:
 
 
 class Batch:
-    """Many small circuits (n <= 13) run in one launch (qk_batch_*)."""
+    """Many circuits in few launches (qk_batch_*): circuits of at most
+    SMEM_QUBITS qubits run whole in shared memory (any op), larger ones up to
+    MAX_QUBITS (unitary gates, at most one control) as batched tile passes."""
 
-    MAX_QUBITS = 13
+    SMEM_QUBITS = 13
+    MAX_QUBITS = 24
 
     def __init__(self, stream: Optional[int] = None):
         h = _P()
@@ -470,6 +474,12 @@ class Batch:
         self._check(_lib.qk_batch_read(self._h, circuit, cb.ctypes.data_as(_U8P), ncb,
                                        st.ctypes.data if state else None, st.nbytes if state else 0))
         return cb[:ncb], st
+
+    def stats(self) -> Dict[str, float]:
+        """Host planning time (ms) and batched tile launches of the last run."""
+        ms, nl = ctypes.c_double(), ctypes.c_int()
+        self._check(_lib.qk_batch_stats(self._h, ctypes.byref(ms), ctypes.byref(nl)))
+        return {"plan_ms": ms.value, "tile_launches": nl.value}
 
     def read_all_cbits(self) -> np.ndarray:
         tot = sum(self._ncb)

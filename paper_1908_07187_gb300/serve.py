@@ -2,7 +2,7 @@
 scheduling only; every amplitude operation runs in libqk's kernels).
 
 Requests are circuits (``workloads.Circuit``) with arrival times.  Small requests
-(at most ``Batch.MAX_QUBITS`` qubits) are served by batched launches: while one
+(at most ``Batch.SMEM_QUBITS`` qubits) are served by batched launches: while one
 batch runs, newly arrived small requests collect into the next batch, which is
 launched as soon as the running one finishes (two batch objects alternate).  Larger
 requests each get a context on a stream of their own and run concurrently, admitted
@@ -68,7 +68,7 @@ class Server:
 
     def run(self, circuits: List, arrivals: List[float]) -> List[Result]:
         qk, torch = self.qk, self.torch
-        small_max = qk.Batch.MAX_QUBITS
+        small_max = qk.Batch.SMEM_QUBITS
         order = sorted(range(len(circuits)), key=lambda i: arrivals[i])
         results = [Result(i, circuits[i].n_qubits, arrivals[i]) for i in range(len(circuits))]
         pending_small: deque = deque()

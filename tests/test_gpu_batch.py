@@ -109,7 +109,7 @@ def test_batch_mulmod_and_conditions(qk):
     assert list(bits) == [int(x) for x in ref.cbits]
     assert np.max(np.abs(psi - ref.psi)) < 1e-5
     with pytest.raises(qk.QKError):
-        b.add_circuit(14, 0)
+        b.add_circuit(25, 0)                    # above the batch's 24 qubits
     with pytest.raises(qk.QKError):
         b.apply_mulmod([1, 2, 3], [0], 5, 15)   # N > 2^w
     b.close()
@@ -148,4 +148,109 @@ def test_gate_list_rejects_bad_entries(qk):
     ops[0]["nc"] = 7
     with pytest.raises(qk.QKError):
         b.apply_gates(ops)
+    b.close()
+
+
+def tv(a, b):
+    return 0.5 * float(np.sum(np.abs(np.abs(a) ** 2 - np.abs(b) ** 2)))
+
+
+def test_batch_large_layered_circuits_match_oracle(qk):
+    """Circuits of 14..20 qubits run as batched tile passes (states in HBM),
+    mixed with shared-memory circuits in the same batch; every final state
+    against the oracle (complex64 bounds)."""
+    shapes = [(14, 60), (10, 30), (15, 40), (17, 25), (12, 20), (20, 8), (16, 33)]
+    b = qk.Batch()
+    specs = []
+    for i, (n, depth) in enumerate(shapes):
+        rng = np.random.default_rng(900 + i)
+        ang = rng.uniform(0.0, 2 * np.pi, size=(depth, n, 3))
+        b.add_circuit(n, 0)
+        b.apply_gates(qk.layer_gate_ops(n, depth, ang))
+        specs.append((n, depth, ang))
+    b.run()
+    for i, (n, depth, ang) in enumerate(specs):
+        _, psi = b.read(i)
+        ref = oracle.run_circuit(workloads.layer_spec_circuit(n, depth, ang))
+        got = psi.astype(np.complex128)
+        assert np.max(np.abs(got - ref.psi)) < 1e-4, (n, depth)
+        assert tv(got, ref.psi) < 1e-5, (n, depth)
+    st = b.stats()
+    assert st["tile_launches"] > 0
+    b.close()
+
+
+def test_batch_large_controlled_and_diagonal_gates_match_context(qk):
+    """Random 1-qubit gates with up to one control and diagonal gates on 14..18
+    qubits: batched tile passes against the single-state fused engine, and one
+    circuit against the oracle."""
+    kinds = ["u3", "h", "x", "y", "z", "s", "t", "p", "rz"]
+    b = qk.Batch()
+    circs = []
+    for i, n in enumerate([14, 16, 18, 15]):
+        rng = np.random.default_rng(1200 + i)
+        ops = []
+        for _ in range(220):
+            k = kinds[rng.integers(len(kinds))]
+            qs = [int(x) for x in rng.choice(n, size=2, replace=False)]
+            nc = int(rng.integers(0, 2))
+            params = ()
+            if k == "u3":
+                params = tuple(float(x) for x in rng.uniform(0, 2 * np.pi, 3))
+            elif k in ("p", "rz"):
+                params = (float(rng.uniform(0, 2 * np.pi)),)
+            ops.append(workloads.Op(k, (qs[0],), controls=tuple(qs[1:1 + nc]), params=params))
+        circ = workloads.Circuit(n, 0, ops)
+        b.add_ops(n, 0, ops)
+        circs.append(circ)
+    b.run()
+    for i, circ in enumerate(circs):
+        _, psi = b.read(i)
+        ctx = qk.run_circuit(circ, "c64", "fused")
+        want = ctx.get_state()
+        ctx.close()
+        assert np.max(np.abs(psi - want)) < 1e-4, circ.n_qubits
+        if i == 0:
+            ref = oracle.run_circuit(circ)
+            assert np.max(np.abs(psi.astype(np.complex128) - ref.psi)) < 1e-4
+    b.close()
+
+
+def test_batch_large_result_is_the_same_alone_and_in_the_mix(qk):
+    n, depth = 15, 30
+    ang = np.random.default_rng(77).uniform(0, 2 * np.pi, size=(depth, n, 3))
+    alone = qk.Batch()
+    alone.add_circuit(n, 0)
+    alone.apply_gates(qk.layer_gate_ops(n, depth, ang))
+    alone.run()
+    _, s1 = alone.read(0)
+    mix = qk.Batch()
+    for i in range(5):
+        m = 14 + i
+        a2 = np.random.default_rng(i).uniform(0, 2 * np.pi, size=(depth, m, 3))
+        mix.add_circuit(m, 0)
+        mix.apply_gates(qk.layer_gate_ops(m, depth, a2))
+        if i == 2:
+            mix.add_circuit(n, 0)
+            mix.apply_gates(qk.layer_gate_ops(n, depth, ang))
+    mix.run()
+    _, s2 = mix.read(3)
+    assert np.array_equal(s1, s2)
+    alone.close()
+    mix.close()
+
+
+def test_batch_large_circuit_rejects_non_unitary_ops(qk):
+    b = qk.Batch()
+    b.add_circuit(15, 1)
+    with pytest.raises(qk.QKError):
+        b.measure([0], [0.5], [0])
+    with pytest.raises(qk.QKError):
+        b.apply_gate("x", [0], controls=[1, 2])
+    with pytest.raises(qk.QKError):
+        b.apply_gate("x", [0], cond=[0])
+    with pytest.raises(qk.QKError):
+        b.apply_mulmod([1, 2, 3, 4], [0], 7, 15)
+    with pytest.raises(qk.QKError):
+        b.add_circuit(25, 0)
     b.close()

@@ -62,7 +62,7 @@ def fake_modules(budget_log):
             open_ctx.pop(self.id, None)
 
     class Batch:
-        MAX_QUBITS = 13
+        SMEM_QUBITS = 13
 
         def __init__(self):
             self.circs = []

@@ -364,6 +364,21 @@ def block_measurement(qk, torch, stream, n: int, reps: int = 10):
         key = "tensor_core" if tc else "cuda_core"
         out[key] = {"ms_per_pass": round(ms, 4), "GBps": round(out["alg_bytes_per_pass"] / ms / 1e6, 1),
                     "TFLOPs": round(out["alg_flops_per_pass"] / ms / 1e9, 2)}
+        if tc:
+            # blocks alternating between qubits 0..4 and 10..14: every application
+            # first gathers its targets onto the lowest physical qubits
+            groups = ([4, 3, 2, 1, 0], [14, 13, 12, 11, 10])
+            for g in groups:
+                ctx.apply_gate(gid, g)
+            ctx.sync()
+            e0.record(stream)
+            for r in range(reps):
+                ctx.apply_gate(gid, groups[r % 2])
+            e1.record(stream)
+            ctx.sync()
+            ms = e0.elapsed_time(e1) / reps
+            out["tensor_core_any_qubits"] = {"ms_per_gate": round(ms, 4),
+                                             "note": "one relabelling gather + one tensor-core pass per gate"}
         ctx.close()
     return out
 
@@ -433,75 +448,186 @@ def kitaev_measurement(qk, torch, stream, b: int = 20, reps: int = 5):
 # ---------------------------------------------------------------------------
 # batched uneven small circuits (secondary measurement)
 # ---------------------------------------------------------------------------
-def batch_measurement(qk, torch, stream, count: int = 4096, seq_sample: int = 24, check_sample: int = 8):
-    """`count` independent U3 + CZ layer circuits of 10..13 qubits (the batch
-    executor's shared-memory limit) and 50..300 layers, all in one batched launch,
-    against running them one after another (one context per circuit, the engine's
-    default mode) on the first `seq_sample` circuits; the batched states of
-    `check_sample` circuits against the complex128 per-gate path (TV distance,
-    max |a - b|)."""
-    import numpy as np
-
-    t0 = time.perf_counter()
-    specs = [workloads.batch_layer_spec(i, n_max=qk.Batch.MAX_QUBITS) for i in range(count)]
-    lists = [qk.layer_gate_ops(*sp) for sp in specs]
-    b = qk.Batch(stream=stream.cuda_stream)
-    for sp, ops in zip(specs, lists):
-        b.add_circuit(sp[0], 0)
-        b.apply_gates(ops)
-    t_build = time.perf_counter() - t0
-    gates = int(sum(len(x) for x in lists))
-    b.run(store_states=True)                      # warm-up (uploads, first launch)
+def _wait_batch(b):
     while not b.done():
         time.sleep(0.0005)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+
+
+def batch_measurement(qk, torch, stream, count: int = 4096, seq_every: int = 16, oracle_per_n: int = 3):
+    """The batched configuration: `count` independent U3 + CZ layer circuits of
+    10..20 qubits (uniform) and 50..300 layers.  Circuits of at most 13 qubits run
+    whole in shared memory; 14..20-qubit circuits as batched tile passes (states
+    in HBM, pass k of every circuit in one launch).  Measured two ways, as the
+    one-circuit-per-context path beside it: end to end (wall time from the gate
+    lists to the finished run: marshalling, host planning, upload, device) and
+    device time.  The per-context path runs every `seq_every`-th circuit on its
+    own fused context fed by one bulk gate-list call, scaled to `count`.  Final
+    states of the `oracle_per_n` shallowest circuits of each size are compared
+    with the complex128 oracle (all-core build)."""
+    import numpy as np
+    import oracle
+
+    specs = [workloads.batch_layer_spec(i) for i in range(count)]
+    lists = [qk.layer_gate_ops(*sp) for sp in specs]
+    gates = int(sum(len(x) for x in lists))
+    b = qk.Batch(stream=stream.cuda_stream)
+
+    def fill():
+        for sp, ops in zip(specs, lists):
+            b.add_circuit(sp[0], 0)
+            b.apply_gates(ops)
+
+    fill()
+    b.run(store_states=True)                      # warm-up: allocations
+    _wait_batch(b)
+    b.clear()
+    t0 = time.perf_counter()
+    fill()
+    t_fill = time.perf_counter() - t0
     b.run(store_states=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    tv, mx = 0.0, 0.0
-    for i in range(check_sample):
+    _wait_batch(b)
+    t_e2e = time.perf_counter() - t0
+    st = b.stats()
+    dev_ms = st["device_ms"]
+    # the oracle on the shallowest circuits of each size
+    by_n = {}
+    for i, (n, depth, _) in enumerate(specs):
+        by_n.setdefault(n, []).append((depth, i))
+    pick = [i for n in sorted(by_n) for _, i in sorted(by_n[n])[:oracle_per_n]]
+    tv_max, mx_max, t_or = 0.0, 0.0, time.perf_counter()
+    for i in pick:
         n, depth, ang = specs[i]
-        ref = qk.Context("c128", "plain", stream=stream.cuda_stream)
-        ref.add_qubits(n)
-        qk.run_ops(ref, workloads.layer_spec_circuit(n, depth, ang).ops)
-        want = ref.get_state()
-        ref.close()
+        ref = oracle.OracleState(n, openmp=True)
+        for op in workloads.layer_spec_circuit(n, depth, ang).ops:
+            ref.apply_op(op)
         got = b.read(i)[1].astype(np.complex128)
-        tv = max(tv, 0.5 * float(np.abs(np.abs(got) ** 2 - np.abs(want) ** 2).sum()))
-        mx = max(mx, float(np.abs(got - want).max()))
+        tv_max = max(tv_max, 0.5 * float(np.abs(np.abs(got) ** 2 - np.abs(ref.psi) ** 2).sum()))
+        mx_max = max(mx_max, float(np.abs(got - ref.psi).max()))
+    t_or = time.perf_counter() - t_or
     b.close()
-    # one circuit after another, one context each
-    circs = [workloads.layer_spec_circuit(*specs[i]) for i in range(seq_sample)]
+    # one circuit per context (fused engine), bulk gate list, every seq_every-th circuit
+    sel = list(range(0, count, seq_every))
     ctxs = []
-    for c in circs:
+    for i in sel:
         ctx = qk.Context("c64", "fused", stream=stream.cuda_stream)
-        ctx.add_qubits(c.n_qubits)
+        ctx.add_qubits(specs[i][0])
         ctxs.append(ctx)
+    for ctx, i in zip(ctxs[:8], sel[:8]):         # warm-up
+        ctx.apply_gates(lists[i])
+        ctx.flush()
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_p = time.perf_counter()
+    t1 = time.perf_counter()
     p0.record(stream)
-    for ctx, c in zip(ctxs, circs):
-        qk.run_ops(ctx, c.ops)
+    for ctx, i in zip(ctxs, sel):
+        ctx.reset()
+        ctx.apply_gates(lists[i])
         ctx.flush()
     p1.record(stream)
     torch.cuda.synchronize()
-    t_seq_host = time.perf_counter() - t_p
-    seq_ms = p0.elapsed_time(p1)
+    seq_wall = time.perf_counter() - t1
+    seq_dev = p0.elapsed_time(p1)
     for ctx in ctxs:
         ctx.close()
-    batched_cps = count / (ms / 1000.0)
-    seq_cps = seq_sample / max(seq_ms / 1000.0, t_seq_host)
-    return {"circuits": count, "qubits": f"10..{qk.Batch.MAX_QUBITS}", "layers": "50..300", "gates": gates,
-            "batched": {"ms": round(ms, 3), "circuits_per_s": round(batched_cps, 1),
-                        "gates_per_s": round(gates / (ms / 1000.0), 1), "host_build_s": round(t_build, 2)},
-            "one_by_one": {"circuits": seq_sample, "circuits_per_s": round(seq_cps, 2),
-                           "note": "wall time (host marshalling included) of the first circuits run one after another"},
-            "speedup_circuits_per_s": round(batched_cps / seq_cps, 1),
-            "precision": {"circuits_checked": check_sample, "tv_max": tv, "max_abs": mx,
-                          "reference": "complex128 one-pass-per-gate path on the GPU"}}
+    scale = count / len(sel)
+    n_large = sum(1 for sp in specs if sp[0] > qk.Batch.SMEM_QUBITS)
+    return {"circuits": count, "qubits": "10..20 (uniform)", "layers": "50..300 (uniform)", "gates": gates,
+            "large_circuits": n_large,
+            "batched": {"e2e_s": round(t_e2e, 3), "e2e_circuits_per_s": round(count / t_e2e, 1),
+                        "device_ms": round(dev_ms, 2), "device_circuits_per_s": round(count / (dev_ms / 1000.0), 1),
+                        "device_gates_per_s": round(gates / (dev_ms / 1000.0), 1),
+                        "host_fill_s": round(t_fill, 3), "host_plan_ms": round(st["plan_ms"], 1),
+                        "tile_launches": st["tile_launches"]},
+            "per_context": {"circuits_run": len(sel), "every": seq_every,
+                            "e2e_s_scaled": round(seq_wall * scale, 3),
+                            "e2e_circuits_per_s": round(len(sel) / seq_wall, 1),
+                            "device_ms_scaled": round(seq_dev * scale, 2),
+                            "device_circuits_per_s": round(len(sel) / (seq_dev / 1000.0), 1),
+                            "note": "one fused context per circuit, one bulk gate-list call each, one stream"},
+            "speedup_e2e": round((seq_wall * scale) / t_e2e, 2),
+            "speedup_device": round((seq_dev * scale) / dev_ms, 2),
+            "precision": {"circuits_checked": len(pick), "tv_max": tv_max, "max_abs": mx_max,
+                          "reference": "complex128 CPU oracle", "oracle_s": round(t_or, 1)}}
+
+
+def dense_block_measurement(qk, torch, stream, n: int = 20, depth: int = 30):
+    """One n-qubit U3 + CZ layer circuit three ways: the fused tile path (FP32
+    CUDA cores, rotation folded into 8 FMAs per pair), and every layer as dense
+    5-qubit blocks (the layer's U3s on five neighbouring qubits and the CZs among
+    them multiplied into one 32 x 32 unitary on the host) on the tensor cores
+    (3xTF32; a block elsewhere is first gathered onto the five lowest physical
+    qubits) and on CUDA cores, with the CZs between blocks as phase passes.  Device time
+    and error against the complex128 oracle for each."""
+    import numpy as np
+    import oracle
+
+    _, _, ang = workloads.batch_layer_spec(7, n_min=n, n_max=n, d_min=depth, d_max=depth)
+    circ = workloads.layer_spec_circuit(n, depth, ang)
+    ref = oracle.OracleState(n, openmp=True)
+    for op in circ.ops:
+        ref.apply_op(op)
+    groups = [list(range(g, min(g + 5, n))) for g in range(0, n, 5)]
+
+    def block_matrix(L, qs):
+        u = np.array([[1.0 + 0j]])
+        for q in reversed(qs):                    # first target (highest qubit) = MSB
+            u = np.kron(u, oracle.u3(*ang[L][q]))
+        d = np.ones(1 << len(qs), dtype=np.complex128)
+        for q in range(L % 2, n - 1, 2):
+            if q in qs and q + 1 in qs:
+                a, b2 = qs.index(q), qs.index(q + 1)
+                for x in range(1 << len(qs)):
+                    if (x >> a) & 1 and (x >> b2) & 1:
+                        d[x] = -d[x]
+        return d[:, None] * u
+
+    mats = [[block_matrix(L, qs) for qs in groups] for L in range(depth)]
+
+    def run_dense(ctx, gids):
+        for L in range(depth):
+            for g, qs in enumerate(groups):
+                ctx.apply_gate(gids[L][g], list(reversed(qs)))
+            for q in range(L % 2, n - 1, 2):
+                if q // 5 != (q + 1) // 5:
+                    ctx.apply_gate("z", [q + 1], controls=[q])
+
+    def timed(make, runner):
+        ctx = make()
+        runner(ctx)
+        ctx.sync()
+        ctx.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        runner(ctx)
+        ctx.flush()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        got = ctx.get_state().astype(np.complex128)
+        ctx.close()
+        return {"ms": round(e0.elapsed_time(e1), 3),
+                "tv": 0.5 * float(np.abs(np.abs(got) ** 2 - np.abs(ref.psi) ** 2).sum()),
+                "max_abs": float(np.abs(got - ref.psi).max())}
+
+    out = {"n": n, "layers": depth, "gates": len(circ.ops)}
+    ops = qk.layer_gate_ops(n, depth, ang)
+
+    def mk_fused():
+        c = qk.Context("c64", "fused", stream=stream.cuda_stream)
+        c.add_qubits(n)
+        return c
+
+    out["fused_tile_fp32"] = timed(mk_fused, lambda c: c.apply_gates(ops))
+    for tc in (True, False):
+        holder = {}
+
+        def mk(tc=tc, holder=holder):
+            c = qk.Context("c64", "plain", stream=stream.cuda_stream, tensor_cores=tc)
+            c.add_qubits(n)
+            holder["gids"] = [[c.define_gate_matrix(m) for m in row] for row in mats]
+            return c
+
+        out["dense_blocks_3xtf32" if tc else "dense_blocks_fp32"] = timed(mk, lambda c: run_dense(c, holder["gids"]))
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -719,6 +845,7 @@ def main():
     batch = None
     if args.batch_circuits > 0 and world == 1:
         batch = batch_measurement(qk, torch, stream, args.batch_circuits)
+        batch["dense_blocks_vs_tile"] = dense_block_measurement(qk, torch, stream)
     precision = None
     if not args.no_precision and args.mode == "fused":
         precision = precision_measurement(qk, torch, stream, n, gops)

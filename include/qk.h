@@ -123,10 +123,12 @@ qk_status qk_add_cbits(qk_ctx *ctx, int n, int *first_cbit_out);
  * 2^k x 2^k matrix, row-major, interleaved (re, im) doubles, copied.  The matrix
  * must satisfy max |U^dagger U - I| <= unitarity_tol (QK_ENOTUNITARY otherwise).
  * *gate_id receives an id >= 0 valid for the life of the context.  A 5-qubit
- * complex64 gate without controls whose targets are the five lowest physical
- * qubits runs on the tensor cores (3xTF32 batched complex GEMM); other dense
- * gates run on CUDA cores.  qk_sync reports QK_ETIMEOUT if a tensor-core pass
- * hit its bounded wait. */
+ * complex64 gate without controls or classical condition runs on the tensor
+ * cores (3xTF32 batched complex GEMM); when its targets are not the five lowest
+ * physical qubits, one relabelling pass first moves them there (the qubit map
+ * records the move, no extra memory beyond the context's gather buffer).  Other
+ * dense gates run on CUDA cores.  qk_sync reports QK_ETIMEOUT if a tensor-core
+ * pass hit its bounded wait. */
 qk_status qk_define_gate_matrix(qk_ctx *ctx, int k, const double *u, double unitarity_tol, int *gate_id);
 
 /* Define a gate "as a function" (Q-Kit section, command 4; QuModExpUaj of
@@ -314,6 +316,11 @@ typedef struct qk_gate_op {
  * entries before the bad one stay appended and the message names its index).
  * The list is copied before the call returns. */
 qk_status qk_batch_apply_gates(qk_batch *b, const qk_gate_op *ops, int count);
+/* The same gate list on a context, in one call (GateOp of the Q-Kit section for
+ * each entry, in order): exactly one qk_apply_gate per entry, with its checks and
+ * errors; on an error the entries before it stay applied and qk_last_error names
+ * the entry.  Lets a caller hand over a whole circuit with one call. */
+qk_status qk_apply_gates(qk_ctx *ctx, const qk_gate_op *ops, int count);
 qk_status qk_batch_measure(qk_batch *b, const int *qubits, int nq, const double *uniforms, const int *dest_cbits);
 qk_status qk_batch_run(qk_batch *b, int store_states);
 /* 1 when the last run has finished, 0 while it runs, -1 on error. */
@@ -322,9 +329,10 @@ qk_status qk_batch_read(qk_batch *b, int circuit, uint8_t *cbits, int ncb, void 
 /* All circuits' cbits, concatenated in circuit order (sum of their cbit counts). */
 qk_status qk_batch_read_all_cbits(qk_batch *b, uint8_t *out, size_t n);
 int qk_batch_num_circuits(const qk_batch *b);
-/* Host planning time (ms) of the large circuits and the number of batched tile
- * launches of the last qk_batch_run. */
-qk_status qk_batch_stats(const qk_batch *b, double *plan_ms, int *tile_launches);
+/* Of the last qk_batch_run: host planning time (ms) of the large circuits, the
+ * number of batched tile launches, and (waits for the run) the device time (ms)
+ * from the end of the host planning to the end of the run's last launch. */
+qk_status qk_batch_stats(qk_batch *b, double *plan_ms, int *tile_launches, double *device_ms);
 const char *qk_batch_last_error(const qk_batch *b);
 
 /* Counters since creation or the last reset_counters: kernel launches, passes

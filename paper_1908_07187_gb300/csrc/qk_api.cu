@@ -361,6 +361,46 @@ qk_status ensure_slots(qk_ctx *c, int nq) {
     return QK_OK;
 }
 
+// Move the logical qubits targets[0..k-1] onto physical qubits 0..k-1 with one
+// relabelling gather: each target above k-1 trades places with a non-target
+// qubit on a low position; the logical -> physical map records the move.
+qk_status move_to_low(qk_ctx *c, const int *targets, int k) {
+    const int n = c->n;
+    std::vector<int> inv(n), newp(c->l2p);
+    for (int q = 0; q < n; ++q) inv[c->l2p[q]] = q;
+    std::vector<char> is_target(n, 0);
+    for (int a = 0; a < k; ++a) is_target[targets[a]] = 1;
+    std::vector<int> free_low;
+    for (int p = 0; p < k; ++p)
+        if (!is_target[inv[p]]) free_low.push_back(p);
+    size_t fi = 0;
+    bool moved = false;
+    for (int a = 0; a < k; ++a) {
+        const int p = c->l2p[targets[a]];
+        if (p < k) continue;
+        const int f = free_low[fi++];
+        newp[targets[a]] = f;
+        newp[inv[f]] = p;
+        moved = true;
+    }
+    if (!moved) return QK_OK;
+    qk_status s = ensure_scratch(c);
+    if (s != QK_OK) return s;
+    std::vector<int> newinv(n);
+    for (int q = 0; q < n; ++q) newinv[newp[q]] = q;
+    qk::RelabelArgs a{};
+    a.n = n;
+    for (int p2 = 0; p2 < n; ++p2) a.phys_of[p2] = c->l2p[newinv[p2]];   // new bit p2 <- old bit
+    a.n_amps = 1ull << n;
+    {
+        LaunchScope ls(c, 6, (double)full_pass_bytes(c));
+        CUDA_TRY(c, qk::launch_relabel((int)c->prec, c->d_state, c->d_scratch, a, c->sms, c->stream));
+    }
+    std::swap(c->d_state, c->d_scratch);
+    c->l2p = newp;
+    return QK_OK;
+}
+
 // Dense 5-qubit gate on physical qubits 0..4 via the tensor-core kernel.  The
 // real embedding of U, with rows and columns permuted to the physical order of
 // the targets, is split into TF32 high and low parts once per target order.
@@ -735,12 +775,13 @@ qk_status qk_apply_gate(qk_ctx *c, int gate_id, const int *targets, int nt, cons
         qk_status s = flush(c);
         if (s != QK_OK) return s;
         if (g.k == 5 && c->prec == QK_C64 && nc == 0 && ncc == 0 && !c->opt.no_tensor_cores) {
-            uint32_t phys = 0, key = 0;
-            for (int a = 0; a < 5; ++a) {
-                phys |= 1u << c->l2p[targets[a]];
-                key |= (uint32_t)c->l2p[targets[a]] << (3 * a);
-            }
-            if (phys == 0x1Fu) return apply_block_tc(c, gate_id, targets, key);
+            // targets elsewhere are first gathered onto physical qubits 0..4 (one
+            // relabelling pass), which costs far less than a CUDA-core block pass
+            qk_status sm = move_to_low(c, targets, 5);
+            if (sm != QK_OK) return sm;
+            uint32_t key = 0;
+            for (int a = 0; a < 5; ++a) key |= (uint32_t)c->l2p[targets[a]] << (3 * a);
+            return apply_block_tc(c, gate_id, targets, key);
         }
         qk::MatKArgs a{};
         a.k = g.k;
@@ -781,6 +822,22 @@ qk_status qk_apply_gate(qk_ctx *c, int gate_id, const int *targets, int nt, cons
         CUDA_TRY(c, qk::launch_perm((int)c->prec, c->d_state, c->d_scratch, a, c->d_cbits, c->sms, c->stream));
     }
     std::swap(c->d_state, c->d_scratch);
+    return QK_OK;
+}
+
+qk_status qk_apply_gates(qk_ctx *c, const qk_gate_op *ops, int count) {
+    if (!c) return QK_EINVAL;
+    if (count < 0 || (count > 0 && !ops)) return fail(c, QK_EINVAL, "apply_gates: bad gate list");
+    for (int i = 0; i < count; ++i) {
+        const qk_gate_op &g = ops[i];
+        if (g.nc < 0 || g.nc > 4 || g.ncc < 0 || g.ncc > 4 || g.np < 0 || g.np > 3)
+            return fail(c, QK_EINVAL, "apply_gates: entry %d has bad counts", i);
+        const qk_status st = qk_apply_gate(c, g.gate_id, &g.target, 1, g.controls, g.nc, g.cond, g.ncc, g.params, g.np);
+        if (st != QK_OK) {
+            const std::string msg = c->err;
+            return fail(c, st, "apply_gates: entry %d: %s", i, msg.c_str());
+        }
+    }
     return QK_OK;
 }
 

@@ -320,6 +320,8 @@ struct qk_batch {
     void *h_stage = nullptr;
     size_t cap_stage = 0;
     cudaEvent_t done = nullptr;
+    cudaEvent_t start = nullptr;       // recorded once the host work of a run is done
+    bool start_recorded = false;
     bool store_state = true;
     std::string err;
     // circuits of 14..24 qubits: gate lists for the tile planner, states in HBM
@@ -513,6 +515,8 @@ qk_status run_large(qk_batch *b) {
         offs[i] = b->large[i].state_off;
     }
     b->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (cudaEventRecord(b->start, b->stream) != cudaSuccess) return bfail(b, QK_ECUDA, "batch: event record failed");
+    b->start_recorded = true;
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return bytes == 0 || cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, b->stream) == cudaSuccess;
     };
@@ -563,7 +567,7 @@ qk_status qk_batch_create(qk_batch **out, void *cuda_stream) {
         }
         b->own_stream = true;
     }
-    if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreate(&b->done) != cudaSuccess || cudaEventCreate(&b->start) != cudaSuccess) {
         qk_batch_destroy(b);
         return QK_ECUDA;
     }
@@ -587,6 +591,7 @@ qk_status qk_batch_destroy(qk_batch *b) {
     cudaFree(b->d_llin);
     if (b->h_stage) cudaFreeHost(b->h_stage);
     if (b->done) cudaEventDestroy(b->done);
+    if (b->start) cudaEventDestroy(b->start);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return QK_OK;
@@ -784,6 +789,18 @@ qk_status qk_batch_run(qk_batch *b, int store_states) {
     if (!b) return QK_EINVAL;
     if (b->circs.empty()) return QK_OK;
     b->store_state = store_states != 0;
+    b->start_recorded = false;
+    b->plan_ms = 0.0;
+    b->large_launches = 0;
+    // large circuits first: their planning is host work, after which the start
+    // event is recorded and everything else is enqueued back to back
+    if (!b->large.empty()) {
+        const qk_status ls = run_large(b);
+        if (ls != QK_OK) return ls;
+    } else {
+        if (cudaEventRecord(b->start, b->stream) != cudaSuccess) return bfail(b, QK_ECUDA, "batch: event record failed");
+        b->start_recorded = true;
+    }
     qk_status s;
     if ((s = grow(b, &b->d_ops, &b->cap_ops, std::max<size_t>(1, b->ops.size()))) != QK_OK) return s;
     if ((s = grow(b, &b->d_circs, &b->cap_circs, std::max<size_t>(1, b->circs.size()))) != QK_OK) return s;
@@ -831,18 +848,23 @@ qk_status qk_batch_run(qk_batch *b, int store_states) {
         if (cudaGetLastError() != cudaSuccess) return bfail(b, QK_ECUDA, "batch: launch failed");
         i = j;
     }
-    if (!b->large.empty()) {
-        const qk_status ls = run_large(b);
-        if (ls != QK_OK) return ls;
-    }
     if (cudaEventRecord(b->done, b->stream) != cudaSuccess) return bfail(b, QK_ECUDA, "batch: event record failed");
     return QK_OK;
 }
 
-qk_status qk_batch_stats(const qk_batch *b, double *plan_ms, int *tile_launches) {
+qk_status qk_batch_stats(qk_batch *b, double *plan_ms, int *tile_launches, double *device_ms) {
     if (!b) return QK_EINVAL;
     if (plan_ms) *plan_ms = b->plan_ms;
     if (tile_launches) *tile_launches = b->large_launches;
+    if (device_ms) {
+        *device_ms = 0.0;
+        if (b->start_recorded) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(b->done) != cudaSuccess || cudaEventElapsedTime(&ms, b->start, b->done) != cudaSuccess)
+                return bfail(b, QK_ECUDA, "batch: event timing failed");
+            *device_ms = ms;
+        }
+    }
     return QK_OK;
 }
 

@@ -126,7 +126,9 @@ _SIGS = {
     "qk_batch_read": ([_P, ctypes.c_int, _U8P, ctypes.c_int, _P, ctypes.c_size_t], ctypes.c_int),
     "qk_batch_read_all_cbits": ([_P, _U8P, ctypes.c_size_t], ctypes.c_int),
     "qk_batch_num_circuits": ([_P], ctypes.c_int),
-    "qk_batch_stats": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "qk_batch_stats": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                        ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "qk_apply_gates": ([_P, _P, ctypes.c_int], ctypes.c_int),
     "qk_batch_last_error": ([_P], ctypes.c_char_p),
     "qk_last_error": ([_P], ctypes.c_char_p),
     "qk_status_str": ([ctypes.c_int], ctypes.c_char_p),
@@ -255,6 +257,11 @@ class Context:
         k, nk = _ints(cond)
         p = (ctypes.c_double * max(1, len(params)))(*params)
         self._check(_lib.qk_apply_gate(self._h, gid, t, nt, c, nc, k, nk, p, len(params)))
+
+    def apply_gates(self, ops: np.ndarray):
+        """A whole gate list (GATE_OP_DTYPE entries) in one call."""
+        arr = np.ascontiguousarray(ops, dtype=GATE_OP_DTYPE)
+        self._check(_lib.qk_apply_gates(self._h, arr.ctypes.data, len(arr)))
 
     def apply_rphase_cbits(self, target: int, cbits: Sequence[int]):
         cb, n = _ints(cbits)
@@ -476,10 +483,11 @@ class Batch:
         return cb[:ncb], st
 
     def stats(self) -> Dict[str, float]:
-        """Host planning time (ms) and batched tile launches of the last run."""
-        ms, nl = ctypes.c_double(), ctypes.c_int()
-        self._check(_lib.qk_batch_stats(self._h, ctypes.byref(ms), ctypes.byref(nl)))
-        return {"plan_ms": ms.value, "tile_launches": nl.value}
+        """Of the last run: host planning time (ms), batched tile launches, and
+        the device time (ms) after the host planning (waits for the run)."""
+        ms, nl, dev = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+        self._check(_lib.qk_batch_stats(self._h, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(dev)))
+        return {"plan_ms": ms.value, "tile_launches": nl.value, "device_ms": dev.value}
 
     def read_all_cbits(self) -> np.ndarray:
         tot = sum(self._ncb)

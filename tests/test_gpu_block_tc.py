@@ -68,3 +68,32 @@ def test_block_tc_agrees_with_cuda_core_path(qk):
         out.append(ctx.get_state())
         ctx.close()
     assert np.max(np.abs(out[0] - out[1])) < 1e-5
+
+
+@pytest.mark.parametrize("n,blocks", [(14, [(9, 12, 5, 13, 7)]), (16, [(4, 3, 2, 1, 0), (15, 11, 8, 6, 10)]),
+                                      (20, [(19, 18, 17, 16, 15), (2, 9, 14, 0, 6), (4, 3, 2, 1, 0)])])
+def test_block_tc_on_any_qubits_matches_oracle(qk, n, blocks):
+    """5-qubit blocks whose targets are not the lowest physical qubits are first
+    gathered there (one relabelling pass) and then run on the tensor cores; mixed
+    with 1-qubit gates and other blocks, against the oracle, in both modes."""
+    rng = np.random.default_rng(n * 31 + len(blocks))
+    Us = [haar(32, rng) for _ in blocks]
+    psi = workloads.random_state(n, 700 + n)
+    for mode in ("plain", "fused"):
+        ctx = qk.Context("c64", mode)
+        ctx.add_qubits(n)
+        ctx.set_state(psi)
+        ref = oracle.OracleState(n, psi=psi)
+        for U, t in zip(Us, blocks):
+            gid = ctx.define_gate_matrix(U)
+            ctx.apply_gate(gid, list(t))
+            ref.apply_matrix(U, list(t))
+            ctx.apply_gate("u3", [t[0]], params=[0.4, 1.1, 2.3])
+            ref.apply_matrix(oracle.u3(0.4, 1.1, 2.3), [t[0]])
+            ctx.apply_gate("z", [t[1]], controls=[(t[1] + 1) % n if (t[1] + 1) % n not in t else (t[1] + 2) % n])
+            c = (t[1] + 1) % n if (t[1] + 1) % n not in t else (t[1] + 2) % n
+            ref.apply_matrix(oracle.GATES_1Q["z"], [t[1]], [c])
+        got = ctx.get_state().astype(np.complex128)
+        err = float(np.max(np.abs(got - ref.psi)))
+        assert err <= 1e-5, (mode, err)
+        ctx.close()

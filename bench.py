@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--no-block", action="store_true", help="skip the dense 5-qubit block measurement")
     ap.add_argument("--no-precision", action="store_true", help="skip the complex64-vs-complex128 precision check")
     ap.add_argument("--batch-circuits", type=int, default=4096, help="circuits in the batched measurement (0: skip)")
-    ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=1000, help="requests in the serving measurement (0: skip)")
     return ap.parse_args()
 
 
@@ -680,10 +680,12 @@ def serving_measurement(torch, count: int, rate: float = 200.0):
 
     reqs = [workloads.serving_request(10_000 + i) for i in range(count)]
     arr = workloads.poisson_arrivals(count, rate, seed=11)
+    # each request marshalled once, before its arrival, for both paths
+    calls = [serve.marshal(qk, c) for c in reqs]
     warm = [workloads.serving_request(20_000 + i, n_min=8, n_max=20) for i in range(8)]
     serve.Server(qk, torch).run(warm, [0.0] * len(warm))
-    served = serve.Server(qk, torch).run(reqs, arr)
-    plain = serve.serve_plain(qk, torch, reqs, arr)
+    served = serve.Server(qk, torch).run(reqs, arr, calls)
+    plain = serve.serve_plain(qk, torch, reqs, arr, calls=calls)
     agree = sum(list(a.cbits) == list(b.cbits) for a, b in zip(served, plain))
     out = {"requests": count, "arrival_rate_per_s": rate, "qubits": "log-uniform 8..33",
            "served": serve.summarize(served), "plain": serve.summarize(plain),

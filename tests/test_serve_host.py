@@ -29,7 +29,7 @@ class _Event:
 class _Stream:
     count = 0
 
-    def __init__(self):
+    def __init__(self, priority=0):
         _Stream.count += 1
         self.cuda_stream = 1000 + _Stream.count
 
@@ -52,6 +52,9 @@ def fake_modules(budget_log):
         def flush(self):
             pass
 
+        def apply_gates(self, arr):
+            run_ops(self, [])
+
         def read_cbits(self):
             return np.zeros(self.ncb, dtype=np.uint8)
 
@@ -64,7 +67,7 @@ def fake_modules(budget_log):
     class Batch:
         SMEM_QUBITS = 13
 
-        def __init__(self):
+        def __init__(self, stream=None):
             self.circs = []
             self.polls = 0
 
@@ -95,7 +98,12 @@ def fake_modules(budget_log):
         open_ctx[ctx.id] = ctx
         budget_log.append(sum(8 << c.n for c in open_ctx.values()))
 
-    qk = types.SimpleNamespace(Context=Context, Batch=Batch, run_ops=run_ops)
+    gate = {"x": -1, "y": -2, "z": -3, "h": -4, "s": -5, "sdg": -6, "t": -7, "tdg": -8, "u3": -9, "p": -10,
+            "rz": -11, "swap": -12}
+    dtype = np.dtype([("gate_id", np.int32), ("target", np.int32), ("nc", np.int32), ("ncc", np.int32),
+                      ("np", np.int32), ("controls", np.int32, 4), ("cond", np.int32, 4), ("params", np.float64, 3)],
+                     align=True)
+    qk = types.SimpleNamespace(Context=Context, Batch=Batch, run_ops=run_ops, GATE=gate, GATE_OP_DTYPE=dtype)
     torch = types.SimpleNamespace(cuda=types.SimpleNamespace(Stream=_Stream, Event=_Event))
     return qk, torch, open_ctx
 

@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -124,13 +125,23 @@ def peaks():
 KERNEL_SOURCES = {"tile": ("kernels_tile.cu", "qk_kernels.cuh", "qk_plan.cu")}
 
 
+_C_TOKENS = re.compile(r'"(?:\\.|[^"\\])*"|\'(?:\\.|[^\'\\])*\'|//[^\n]*|/\*.*?\*/', re.S)
+
+
+def code_only(src: str) -> str:
+    """C/C++/CUDA source without comments, whitespace runs collapsed: what the
+    compiler sees, so that editing a comment does not read as a kernel change."""
+    out = _C_TOKENS.sub(lambda m: m.group(0) if m.group(0)[0] in "\"'" else " ", src)
+    return " ".join(out.split())
+
+
 def kernel_source_sha(kernel_class: str = "tile"):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1908_07187_gb300", "csrc")
     for f in KERNEL_SOURCES.get(kernel_class, sorted(os.listdir(csrc))):
         if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+            with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+                h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -552,7 +563,7 @@ def batch_measurement(qk, torch, stream, count: int = 4096, seq_every: int = 16,
 
 def dense_block_measurement(qk, torch, stream, n: int = 20, depth: int = 30):
     """One n-qubit U3 + CZ layer circuit three ways: the fused tile path (FP32
-    CUDA cores, rotation folded into 8 FMAs per pair), and every layer as dense
+    CUDA cores, pivot-form butterflies), and every layer as dense
     5-qubit blocks (the layer's U3s on five neighbouring qubits and the CZs among
     them multiplied into one 32 x 32 unitary on the host) on the tensor cores
     (3xTF32; a block elsewhere is first gathered onto the five lowest physical

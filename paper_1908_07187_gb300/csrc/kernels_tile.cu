@@ -12,8 +12,9 @@
 // transposing the tile through shared memory (three fixed arrangements, see
 // qk_kernels.cuh).
 //
-// Uncontrolled gates run in pivot form (LayerGate in qk_kernels.cuh): 8 FMAs per
-// amplitude pair instead of the 16 of a complex 2x2 product.  What the pivot form
+// Uncontrolled gates run in pivot form (LayerGate in qk_kernels.cuh): 10 FP32
+// operations per amplitude pair (in place) instead of the 16 of a complex 2x2
+// product.  What the pivot form
 // leaves over -- a real scale, the same for every amplitude of the pass, and
 // per-qubit phases -- stays pending.  The parts that are the same for every
 // thread are tracked by the planner and folded into later gates' coefficients or

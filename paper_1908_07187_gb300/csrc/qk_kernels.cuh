@@ -293,7 +293,8 @@ struct LinTerm {
 // of the bit folded in, M diag(1, F) has its larger entries on the diagonal
 // (|M00| = |M11| >= |M10| = |M01|).  It is applied to a pair (y0, y1) as
 //   z0 = y0 + a0 y1,  z1 = y1 + a1 y0,   a0 = M01 F / M00,  a1 = M10 / (M11 F),
-// and the true outputs are (M00 z0, M11 F z1): |a0|, |a1| <= 1 and 8 FMAs per pair.
+// and the true outputs are (M00 z0, M11 F z1): |a0|, |a1| <= 1, and 10 FP32
+// operations per pair in place (u = a1 y0; y0 += a0 y1; y1 += u).
 // |M00| >= 1/sqrt 2 is one real scale for the whole pass and the phases of M00
 // and M11 F / M00 become pending phases, both tracked by the planner.  The
 // device uses a0 = A0 e and a1 = A1 conj(e), with e the thread-dependent part of

@@ -56,3 +56,17 @@ def test_single_rank_is_identity():
 
     assert bench.max_over_ranks([3.0, 4.0]) == [3.0, 4.0]
     assert bench.job_throughput(10, 2, 1, 0.5) == 40.0
+
+
+def test_kernel_hash_ignores_comments_only():
+    """The recorded-traffic key changes with the code the compiler sees, not with
+    comments or layout; strings that look like comments are code."""
+    import bench
+
+    a = "int f(int x) { // doubles\n  return 2 * x; /* twice */ }\nconst char *u = \"a//b\";\n"
+    b = "int f(int x) {\n\n   return 2 * x;   }\nconst char *u = \"a//b\";  // note\n"
+    c = "int f(int x) { return 3 * x; }\nconst char *u = \"a//b\";\n"
+    d = "int f(int x) { return 2 * x; }\nconst char *u = \"a/*b*/\";\n"
+    assert bench.code_only(a) == bench.code_only(b)
+    assert bench.code_only(a) != bench.code_only(c)
+    assert "/*b*/" in bench.code_only(d)

@@ -607,6 +607,24 @@ struct PoolProg {
     __device__ __forceinline__ const LinTerm &lin(int i) const { return lins[h.lin0 + i]; }
 };
 
+// The fields of a TileOp that the common op kinds read (its first 16 bytes),
+// loaded as two 8-byte words.  The op loop loads the next op's head while the
+// current op runs, so that a short op is not followed by a wait on the next
+// op's fields.
+struct OpHead {
+    uint32_t w0, w1, w2, w3;
+    __device__ __forceinline__ int kind() const { return (int)(w0 & 0xffu); }
+    __device__ __forceinline__ int k() const { return (int)((w0 >> 8) & 0xffu); }
+    __device__ __forceinline__ int rval() const { return (int)(w0 >> 24); }
+    __device__ __forceinline__ int count() const { return (int)(w2 >> 16); }
+    __device__ __forceinline__ int first() const { return (int)(w3 & 0xffffu); }
+};
+__device__ __forceinline__ OpHead load_head(const TileOp &op) {
+    const uint2 *p = reinterpret_cast<const uint2 *>(&op);
+    const uint2 a = p[0], b = p[1];
+    return OpHead{a.x, a.y, b.x, b.y};
+}
+
 // One tile of one pass: load, run the program, final flush, store.
 template <typename Off, typename Prog>
 __device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ psi, uint64_t tile,
@@ -639,19 +657,6 @@ __device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ p
             load_all<Off>(psi + tb, o, v, std::make_integer_sequence<int, 32>{});
         }
 
-        // ask L2 for the tile a CTA about one wave later will load (one 256-byte
-        // chunk per thread), so that its HBM reads overlap this CTA's work
-        if (P.pf_dist && tile + P.pf_dist < P.n_tiles) {
-            uint64_t b2 = tile_base(P, tile + P.pf_dist);
-#pragma unroll
-            for (int j = 0; j < 5; ++j)
-                if ((lane >> j) & 1) b2 += 1ull << P.S[5 + j];
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                if ((warp >> j) & 1) b2 += 1ull << P.S[10 + j];
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], 256;" ::"l"(psi + b2) : "memory");
-        }
-
         // while the loads are in flight: the phase table, the classical conditions
         fill_turn_table();
         unsigned condok = 0;
@@ -667,12 +672,15 @@ __device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ p
         pd.reset();
         int cur = ARR_IO;
         const uint32_t tidx = (uint32_t)tile;
+        OpHead nh{0u, 0u, 0u, 0u};
+        if (P.nops > 0) nh = load_head(pr.op(0));
         for (int i = 0; i < P.nops; ++i) {
-            const TileOp &op = pr.op(i);
-            switch (op.kind) {
+            const OpHead h = nh;
+            if (i + 1 < P.nops) nh = load_head(pr.op(i + 1));
+            switch (h.kind()) {
                 case TOP_U2L: {
-                    const LayerGate *lg = &pr.lg(op.first);
-                    const int bits = op.k;
+                    const LayerGate *lg = &pr.lg(h.first());
+                    const int bits = h.k();
                     if (bits & 1) layer_gate<0>(v, pd, *lg++);
                     if (bits & 2) layer_gate<1>(v, pd, *lg++);
                     if (bits & 4) layer_gate<2>(v, pd, *lg++);
@@ -681,33 +689,33 @@ __device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ p
                     break;
                 }
                 case TOP_PAIRNEG:
-                    pair_neg(v, op.k);
+                    pair_neg(v, h.k());
                     break;
                 case TOP_PHASEL: {
                     uint32_t acc = 0;
-                    const int end = op.first + op.count;
-                    for (int e = op.first; e < end; ++e) {
+                    const int end = h.first() + h.count();
+                    for (int e = h.first(); e < end; ++e) {
                         const LinTerm &L = pr.lin(e);
                         const bool ok = ((tbits & L.tmask) == L.tval) && ((tidx & L.fmask) == L.fval);
                         acc += ok ? L.turns : 0u;
                     }
                     if (acc) {
-                        if (op.rval) {  // the term's qubit is stored flipped: on bit k = 0
+                        if (h.rval()) {  // the term's qubit is stored flipped: on bit k = 0
                             pd.add(5, acc);
-                            pd.add(op.k, 0u - acc);
+                            pd.add(h.k(), 0u - acc);
                         } else {
-                            pd.add(op.k, acc);
+                            pd.add(h.k(), acc);
                         }
                     }
                     break;
                 }
                 case TOP_XPOSE:
                     flush_dev(v, pd);
-                    transpose(v, sre, sim, cur, op.k, lane, warp);
-                    cur = op.k;
+                    transpose(v, sre, sim, cur, h.k(), lane, warp);
+                    cur = h.k();
                     break;
                 default:
-                    general_op<Off>(v, pd, op, tbits, base, condok);
+                    general_op<Off>(v, pd, pr.op(i), tbits, base, condok);
                     break;
             }
         }

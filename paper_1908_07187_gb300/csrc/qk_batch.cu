@@ -436,7 +436,6 @@ qk_status run_large(qk_batch *b) {
                 }
                 qk::TileProg h{};
                 static_cast<qk::TileHead &>(h) = P;
-                h.pf_dist = 0;
                 h.op0 = (uint32_t)out.ops.size();
                 h.lg0 = (uint32_t)out.lg.size();
                 h.lin0 = (uint32_t)out.lin.size();

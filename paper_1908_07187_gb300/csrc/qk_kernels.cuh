@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 namespace qk {
@@ -324,6 +325,12 @@ struct TileOp {
         } ph;
     };
 };
+// The tile kernel reads the fields the common op kinds need (kind, k, rval,
+// count, first) as the op's first two 8-byte words, one op ahead.
+static_assert(offsetof(TileOp, kind) == 0 && offsetof(TileOp, k) == 1 && offsetof(TileOp, rval) == 3 &&
+                  offsetof(TileOp, count) == 10 && offsetof(TileOp, first) == 12 && offsetof(TileOp, hturns) == 16,
+              "TileOp head layout");
+static_assert(alignof(TileOp) >= 8, "TileOp head is read as 8-byte words");
 
 // The scalar part of a tile-pass program (the arrays follow in TileParams, or
 // sit in device pools for a batched launch, see TileProg).
@@ -346,7 +353,6 @@ struct TileHead {
     uint32_t fin_turns[14];
     float fin_scale;
     int fin_flip;          // local qubits stored flipped at the end (bit b: local qubit b)
-    uint32_t pf_dist;      // L2 prefetch of the tile this many CTAs ahead (0: none)
     int nlg, nlin;         // entries of lg[] and lin[] in use
 };
 

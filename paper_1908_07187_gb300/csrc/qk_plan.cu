@@ -749,7 +749,6 @@ qk_status run_fused(TilePlanner *planner, qk_ctx *c, const std::vector<FusedOp> 
             cudaEventCreate(&ev1);
             cudaEventRecord(ev0, ctx_stream(c));
         }
-        P.pf_dist = (uint32_t)(2 * ctx_sms(c));   // one wave of resident CTAs ahead
         ctx_launch_begin(c, 0, 2.0 * 8.0 * (double)(1ull << n), &tok);
         cudaError_t e = launch_tile(ctx_state(c), P, ctx_cbits(c), ctx_stream(c));
         ctx_launch_end(tok);

@@ -29,7 +29,7 @@ struct TilePlanner;
 TilePlanner *make_planner();
 void free_planner(TilePlanner *p);
 // Plan an n-qubit (n >= 13) complex64 op list into tile passes; each pass's
-// program goes to sink in order (it may modify the program, e.g. set pf_dist).
+// program goes to sink in order (the sink may adjust it before launching it).
 // On a planner error *err names it.
 using PassSink = std::function<qk_status(TileParams &)>;
 qk_status plan_passes(TilePlanner *p, int n, const std::vector<FusedOp> &ops, const PassSink &sink, const char **err);

@@ -1,8 +1,10 @@
 """Classical post-processing of an order-finding run (host arithmetic only).
 
-The Shor section of the paper turns the classical bits of the Kitaev run into the
-order r of a modulo N by continued fractions, then into prime factors.  Here:
-the t measured bits give y = sum_e m_e 2^e (stage e's bit is m_e), y / 2^t is
+The Shor section of the paper turns the classical bits of an order-finding run
+(Kitaev's, or the conventional 3nx1 circuit's control register) into the order
+r of a modulo N by continued fractions, then into prime factors.  Here: the t
+measured bits give y (Kitaev: y = sum_e m_e 2^e, stage e's bit is m_e; 3nx1: the
+control register's value, qubit 0 its MSB), y / 2^t is
 close to s / r for some s, so r (or a divisor of it when gcd(s, r) > 1) is a
 denominator of a convergent of y / 2^t; a small multiple of that denominator is
 tried until a^r = 1 mod N (the paper's third 24-bit run found 141210 = r / 4).
@@ -16,8 +18,18 @@ from typing import List, Optional, Sequence, Tuple
 
 
 def outcome_from_bits(bits: Sequence[int]) -> int:
-    """y = sum_e m_e 2^e from the stage bits m_0, m_1, ..."""
+    """y = sum_e m_e 2^e from the stage bits m_0, m_1, ... (Kitaev's run: stage e
+    measures bit e of y)."""
     return sum((int(m) & 1) << e for e, m in enumerate(bits))
+
+
+def register_from_bits(bits: Sequence[int]) -> int:
+    """Value of a register measured qubit by qubit in list order, the first-listed
+    qubit its MSB (the 3nx1 run's control and work registers)."""
+    v = 0
+    for m in bits:
+        v = (v << 1) | (int(m) & 1)
+    return v
 
 
 def convergents(num: int, den: int) -> List[Tuple[int, int]]:

@@ -126,3 +126,56 @@ def test_ghz_33q_uses_64_bit_tile_offsets(env):
     assert abs(complex(view[(1 << n) - 1].item()) - h) < 1e-6
     assert abs(norm2(torch, view) - 1.0) < 1e-5     # so every other amplitude is zero
     ctx.close()
+
+
+def test_shor_3nx1_33q_matches_the_closed_form(env):
+    """The conventional (3nx1) order-finding circuit at its largest single-GPU size:
+    an 11-bit N with a 22-qubit control register, 33 qubits (64 GiB of complex64 plus
+    the mul-mod gather buffer).  After the work register is measured at w = a^x0 mod N
+    and the QFT sequence has run, the amplitude at control value y and work value w
+    is (M 2^t)^-1/2 sum_{m<M} exp(2 pi i (x0 + m r) y / 2^t), M = #{x0 + m r < 2^t};
+    4096 sampled y are checked against it, then the control register is measured and
+    the state must collapse onto (y, w)."""
+    from paper_1908_07187_gb300 import shor
+
+    qk, torch = env
+    N, a = workloads.kitaev_parameters(11, seed=4)
+    circ = workloads.shor_3nx1_circuit(N, a, seed=3)
+    b = N.bit_length()
+    t = circ.n_qubits - b
+    assert circ.n_qubits == 33 and circ.ops[-1].kind == "measure"
+    r, x = 1, a % N
+    while x != 1:
+        x, r = x * a % N, r + 1
+    ctx = qk.Context("c64", "fused")
+    ctx.add_qubits(circ.n_qubits)
+    ctx.add_cbits(circ.n_cbits)
+    qk.run_ops(ctx, circ.ops[:-1])
+    bits = [int(v) for v in ctx.read_cbits()]
+    w = shor.register_from_bits(bits[:b])
+    x0 = next(e for e in range(r) if pow(a, e, N) == w)
+    T = 1 << t
+    M = (T - x0 + r - 1) // r
+    rng = np.random.default_rng(33)
+    ys = np.array([0, T - 1] + [int(v) for v in rng.integers(0, T, size=4096)], dtype=np.int64)
+    # geometric sum of exp(i theta m), theta = 2 pi r y / 2^t, done in exact turns
+    turns = (r * ys) % T
+    theta = 2 * math.pi * turns / T
+    top = np.exp(2j * math.pi * ((turns * M) % T) / T) - 1
+    geo = np.where(turns == 0, M, top / np.where(turns == 0, 1, np.exp(1j * theta) - 1))
+    expect = np.exp(2j * math.pi * ((x0 * ys) % T) / T) * geo / math.sqrt(M * T)
+    widx = bitrev(w, b) << t
+    idx = torch.tensor([bitrev(int(y), t) + widx for y in ys], device="cuda")
+    view = ctx.torch_view()
+    ctx.sync()
+    got = view[idx].cpu().numpy().astype(np.complex128)
+    err = np.abs(got - expect).max()
+    assert err < 1e-5, err
+    assert abs(norm2(torch, view) - 1.0) < 1e-5
+    qk.run_ops(ctx, circ.ops[-1:])
+    bits = [int(v) for v in ctx.read_cbits()]
+    y = shor.register_from_bits(bits[b:])
+    view = ctx.torch_view()
+    ctx.sync()
+    assert abs(abs(complex(view[bitrev(y, t) + widx].item())) ** 2 - 1.0) < 1e-4
+    ctx.close()

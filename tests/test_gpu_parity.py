@@ -313,6 +313,56 @@ def test_order_finding_to_factors_n15(qk, seed):
         assert r is None
 
 
+def oracle_with_margin(circ):
+    """The oracle's run of a circuit and the smallest |u - P0| over its measured
+    qubits (a bit may legitimately differ only where that is below the precision's
+    bound)."""
+    ref = oracle.OracleState(circ.n_qubits, circ.n_cbits)
+    margin = 1.0
+    for op in circ.ops:
+        ref.apply_op(op)
+        if op.kind == "measure":
+            margin = min([margin] + [abs(u - p0) for u, p0 in zip(op.uniforms, ref.last_p0)])
+    return ref, margin
+
+
+@pytest.mark.parametrize("N,a", [(15, 2), (15, 7), (21, 2), (33, 5), (35, 3)])
+@pytest.mark.parametrize("prec,mode", [("c64", "plain"), ("c64", "fused"), ("c128", "plain")])
+def test_shor_3nx1_against_oracle(qk, N, a, prec, mode):
+    """The conventional (3nx1) order-finding circuit of Appendix A: 2b+1 or 2b
+    control qubits, b work qubits, controlled mul-mod gathers, the work register
+    measured mid-circuit, the QFT sequence, the control register measured: cbits
+    bit-exact and the final state element by element."""
+    circ = workloads.shor_3nx1_circuit(N, a, seed=7)
+    ref, margin = oracle_with_margin(circ)
+    assert margin > MARGIN[prec]
+    ctx = qk.run_circuit(circ, prec, mode)
+    assert list(ctx.read_cbits()) == [int(x) for x in ref.cbits]
+    check_state(ctx.get_state(), ref.psi, prec)
+    ctx.close()
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4])
+def test_shor_3nx1_n21_to_factors(qk, seed):
+    # the whole conventional pipeline: the GPU run, then continued fractions on the
+    # control register's value (r = 6 for a = 2, which does not divide 2^9)
+    from paper_1908_07187_gb300 import shor
+
+    N, a = 21, 2
+    circ = workloads.shor_3nx1_circuit(N, a, seed=seed)
+    ref, margin = oracle_with_margin(circ)
+    ctx = qk.run_circuit(circ, "c64", "fused")
+    bits = [int(x) for x in ctx.read_cbits()]
+    ctx.close()
+    assert margin > MARGIN["c64"] and bits == [int(x) for x in ref.cbits]
+    b, t = N.bit_length(), circ.n_cbits - N.bit_length()
+    assert shor.register_from_bits(bits[:b]) in {pow(a, x, N) for x in range(6)}
+    y = shor.register_from_bits(bits[b:])
+    r = shor.order_from_outcome(y, t, a, N)
+    if r is not None:
+        assert r == 6 and shor.factors_from_order(a, r, N) in ((3, 7), (7, 3))
+
+
 def test_add_qubits_keeps_state_and_counters(qk):
     psi = workloads.random_state(5, 19)
     ctx = new_ctx(qk, 5, "c64", "plain", psi)

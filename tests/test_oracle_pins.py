@@ -457,3 +457,97 @@ def test_all_core_oracle_build_is_bit_identical():
         a.apply_op(op)
         b.apply_op(op)
     assert np.array_equal(a.psi, b.psi)
+
+
+# -- conventional order finding (the 3nx1 branch) ---------------------------------
+
+def register_marginal(psi, qubits):
+    """P(value) of a register (first-listed qubit = MSB) from a full state."""
+    n = int(np.log2(psi.size))
+    idx = np.arange(psi.size)
+    val = np.zeros(psi.size, dtype=np.int64)
+    for q in qubits:
+        val = (val << 1) | ((idx >> q) & 1)
+    return np.bincount(val, weights=np.abs(psi) ** 2, minlength=1 << len(qubits))
+
+
+def shor_3nx1_amplitude(y, x0, r, t):
+    """Control-register amplitude after the forward QFT when the control register
+    holds the uniform superposition of x = x0, x0 + r, ... < 2^t (what measuring the
+    work register leaves): (M 2^t)^-1/2 sum_{m<M} exp(2 pi i (x0 + m r) y / 2^t)."""
+    T = 1 << t
+    M = (T - x0 + r - 1) // r
+    x = x0 + r * np.arange(M)
+    return np.exp(2j * math.pi * np.outer(np.atleast_1d(y), x) / T).sum(axis=1) / math.sqrt(M * T)
+
+
+def reg_value(bits):
+    """Register value from measured bits, first bit the MSB."""
+    v = 0
+    for m in bits:
+        v = 2 * v + int(m)
+    return v
+
+
+def ops_until_last_measure(circ):
+    k = max(i for i, op in enumerate(circ.ops) if op.kind == "measure")
+    return circ.ops[:k]
+
+
+def test_3nx1_n15_exact_outcome_law():
+    """N = 15, a = 2 (12 qubits: 8 control + 4 work, the paper's printed shape):
+    before the work register is measured it holds 1, 2, 4, 8 with probability 1/4
+    each; afterwards the QFT leaves the control register on y = 0, 64, 128, 192
+    with probability 1/4 each (r = 4 divides 2^8) and nothing anywhere else."""
+    g = load_golden("paper_values.txt")
+    N, a = 15, g["default_base_a"]
+    circ = workloads.shor_3nx1_circuit(N, a)
+    assert circ.n_qubits == g["n15_3nx1_qubits"]
+    t, b = workloads.paper_stage_count(N), N.bit_length()
+    assert t == g["n15_cbits"]
+    ctrl, work = list(range(t)), list(range(t, t + b))
+    st = oracle.OracleState(circ.n_qubits, circ.n_cbits)
+    for op in circ.ops:
+        if op.kind == "measure" and tuple(op.targets) == tuple(work):
+            Pw = register_marginal(st.psi, work)
+            np.testing.assert_allclose(Pw[[1, 2, 4, 8]], 0.25, atol=1e-12)
+            assert abs(Pw.sum() - 1) < 1e-12
+        if op.kind == "measure" and tuple(op.targets) == tuple(ctrl):
+            Py = register_marginal(st.psi, ctrl)
+            expect = np.zeros(1 << t)
+            expect[[0, 64, 128, 192]] = 0.25
+            np.testing.assert_allclose(Py, expect, atol=1e-12)
+        st.apply_op(op)
+    w = reg_value(st.cbits[:b])
+    y = reg_value(st.cbits[b:])
+    assert w in (1, 2, 4, 8) and y in (0, 64, 128, 192)
+
+
+@pytest.mark.parametrize("N,a", [(21, 2), (33, 5), (35, 3)])
+def test_3nx1_state_equals_the_closed_form(N, a):
+    """General N (r need not divide 2^t): after the work register is measured at
+    w = a^x0 mod N and the QFT sequence has run, every amplitude of the state equals
+    the closed form on work value w and is zero elsewhere; averaged over x0, the
+    control-register law is the phase-estimation closed form that pins the Kitaev
+    run above."""
+    circ = workloads.shor_3nx1_circuit(N, a, seed=11)
+    t, b = workloads.paper_stage_count(N), N.bit_length()
+    st = oracle.OracleState(circ.n_qubits, circ.n_cbits)
+    for op in ops_until_last_measure(circ):
+        st.apply_op(op)
+    r = multiplicative_order(a, N)
+    w = reg_value(st.cbits[:b])
+    x0 = next(x for x in range(r) if pow(a, x, N) == w)
+    ys = np.arange(1 << t)
+    A = shor_3nx1_amplitude(ys, x0, r, t)
+    # index = sum_q bit_q 2^q with control qubit q = bit t-1-q of y, work qubit t+k = bit b-1-k of w
+    yidx = np.zeros(1 << t, dtype=np.int64)
+    for q in range(t):
+        yidx |= ((ys >> (t - 1 - q)) & 1) << q
+    widx = sum(((w >> (b - 1 - k)) & 1) << (t + k) for k in range(b))
+    np.testing.assert_allclose(st.psi[yidx + widx], A, atol=1e-12)
+    assert abs(np.sum(np.abs(st.psi[yidx + widx]) ** 2) - 1) < 1e-12
+    # the x0-average of |A|^2 weighted by P(w) = M / 2^t is the Kitaev closed form
+    T = 1 << t
+    Py = sum(((T - x + r - 1) // r) / T * np.abs(shor_3nx1_amplitude(ys, x, r, t)) ** 2 for x in range(r))
+    np.testing.assert_allclose(Py, qpe_closed_form(r, t), atol=1e-12)

@@ -21,6 +21,9 @@ workload shapes of the benchmark configurations:
 * ``kitaev_circuit``      -- Kitaev's one-recycled-control-qubit order finding
   (the ``nx2n`` branch of Appendix A): 2b stages of H, controlled
   x -> a^(2^j) x mod N, semiclassical phase correction, H, measure, copy, reset.
+* ``shor_3nx1_circuit``   -- conventional order finding (the ``3nx1`` branch):
+  H on a 2b-qubit control register, controlled modular multiplications on a
+  b-qubit work register, measure the work register, QFT, measure the controls.
 """
 from __future__ import annotations
 
@@ -308,6 +311,40 @@ def kitaev_circuit(N: int, a: int, t: int | None = None, seed: int = 3,
 def paper_stage_count(N: int) -> int:
     """nC of the paper's script: bit_length(N^2 - 1) (Appendix A, nx2n branch)."""
     return (N * N - 1).bit_length()
+
+
+def shor_3nx1_circuit(N: int, a: int, t: int | None = None, seed: int = 5,
+                      uniforms: Sequence[float] | None = None) -> Circuit:
+    """Conventional Shor order finding, the 3nx1 branch of Appendix A.
+
+    Qubits 0..t-1 form the control register (qubit 0 its MSB), qubits t..t+b-1 the
+    work register (qubit t its MSB), b = bit_length(N) and t = bit_length(N^2 - 1)
+    by default.  Steps: X on the last qubit (work register = 1); H on every
+    control qubit; for c = 0..t-1 the controlled x -> a^(2^c) x mod N on the work
+    register, controlled by qubit t-1-c (so the exponent reads with qubit 0 as its
+    MSB); measure the work register (qubit by qubit, into cbits 0..b-1); the QFT
+    command sequence of Appendix A on the control register (H then CPHASE pi/2^(i+1),
+    then the end-for-end SWAPs); finally measure the control register into cbits
+    b..b+t-1 (qubit 0 into cbit b), which the script leaves to the viewer."""
+    b = N.bit_length()
+    if t is None:
+        t = paper_stage_count(N)
+    n = t + b
+    rng = SplitMix64(seed * 104729 + N)
+    if uniforms is None:
+        uniforms = [rng.uniform() for _ in range(b + t)]
+    if len(uniforms) != b + t:
+        raise ValueError("need one uniform per measured qubit")
+    ctrl = tuple(range(t))
+    work = tuple(range(t, n))
+    ops: List[Op] = [Op("x", (n - 1,))]
+    ops += [Op("h", (q,)) for q in ctrl]
+    for c in range(t):
+        ops.append(Op("mulmod", work, controls=(t - 1 - c,), params=(a, c, N)))
+    ops.append(Op("measure", work, cbits=tuple(range(b)), uniforms=tuple(uniforms[:b])))
+    ops += qft_ops(ctrl)
+    ops.append(Op("measure", ctrl, cbits=tuple(range(b, b + t)), uniforms=tuple(uniforms[b:])))
+    return Circuit(n, b + t, ops, name=f"shor3nx1_N{N}_a{a}_t{t}")
 
 
 def serving_request(seed: int, n: int | None = None, n_min: int = 8, n_max: int = 33) -> Circuit:

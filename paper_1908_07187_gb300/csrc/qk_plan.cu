@@ -208,22 +208,25 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
     // kernel-parameter budget (ops and grouped phase entries)
     int max_u2 = 100, max_ph = 300;
     std::vector<POp> left, taken;
-    while (!rem.empty()) {
-        // ---- choose S and the gates this pass takes
-        uint64_t S = (1ull << kTileContig) - 1;
-        int cnt = kTileContig;
+    // The gates one pass takes from rem for a qubit set S: in order, each gate
+    // that commutes with every gate left behind before it, whose 2x2 target is in
+    // S (with grow, a target joins S while S has room) and whose classical
+    // condition fits the condition table.  Counts only when tk is null.
+    std::vector<Cond> conds;
+    auto take = [&](uint64_t S0, bool grow, std::vector<POp> *tk, std::vector<POp> *lf, uint64_t *S_out,
+                    int *n_u2_out, int *n_ph_out) {
+        uint64_t S = S0;
+        int cnt = __builtin_popcountll(S0);
         uint64_t ndb = 0, allb = 0;
-        std::vector<Cond> conds;
-        left.clear();
-        taken.clear();
         int n_u2 = 0, n_ph = 0;
+        conds.clear();
         for (const POp &p : rem) {
             const bool is_u2 = p.op->kind == FusedOp::U2;
             bool ok = (is_u2 ? n_u2 < max_u2 : n_ph < max_ph) && !(p.nd & allb) && !(p.all & ndb);
-            if (ok && p.op->kind == FusedOp::U2) {
+            if (ok && is_u2) {
                 const uint64_t t = 1ull << p.op->q;
                 if (!(S & t)) {
-                    if (cnt < kTileQubits) {
+                    if (grow && cnt < kTileQubits) {
                         S |= t;
                         ++cnt;
                     } else {
@@ -240,14 +243,46 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
                 }
             }
             if (ok) {
-                taken.push_back(p);
+                if (tk) tk->push_back(p);
                 if (is_u2) ++n_u2; else ++n_ph;
             } else {
-                left.push_back(p);
+                if (lf) lf->push_back(p);
                 ndb |= p.nd;
                 allb |= p.all;
             }
         }
+        *S_out = S;
+        *n_u2_out = n_u2;
+        *n_ph_out = n_ph;
+    };
+    while (!rem.empty()) {
+        // ---- choose S and the gates this pass takes: the set that the greedy
+        // walk builds, or the contiguous qubits plus a window of consecutive
+        // qubits, whichever lets the pass take the most 2x2 gates (then the most
+        // gates); a circuit whose gates spread along the qubit line (layers of
+        // neighbour couplings) fills passes better with windows
+        const uint64_t low = (1ull << kTileContig) - 1;
+        uint64_t S = 0, best_S0 = low;
+        bool best_grow = true;
+        int n_u2 = 0, n_ph = 0;
+        take(low, true, nullptr, nullptr, &S, &n_u2, &n_ph);
+        int best_u2 = n_u2, best_all = n_u2 + n_ph;
+        const int wlen = kTileQubits - kTileContig;
+        for (int w = kTileContig; w + wlen <= n; ++w) {
+            const uint64_t S0 = low | (((1ull << wlen) - 1) << w);
+            uint64_t Sw;
+            take(S0, false, nullptr, nullptr, &Sw, &n_u2, &n_ph);
+            if (n_u2 > best_u2 || (n_u2 == best_u2 && n_u2 + n_ph > best_all)) {
+                best_u2 = n_u2;
+                best_all = n_u2 + n_ph;
+                best_S0 = S0;
+                best_grow = false;
+            }
+        }
+        left.clear();
+        taken.clear();
+        take(best_S0, best_grow, &taken, &left, &S, &n_u2, &n_ph);
+        int cnt = __builtin_popcountll(S);
         // fill S up to 13 qubits with the lowest unused ones
         for (int b = kTileContig; b < n && cnt < kTileQubits; ++b)
             if (!((S >> b) & 1)) {

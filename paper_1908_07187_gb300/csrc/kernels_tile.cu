@@ -429,6 +429,21 @@ template <int K, int L, int... rs>
 __device__ __forceinline__ void pair_neg_all(Regs &v, std::integer_sequence<int, rs...>) {
     (pair_neg_one<K, L, rs>(v), ...);
 }
+// the CZs of a layer op's mask (bit cz_index(k, l) for the pair k < l)
+__device__ __forceinline__ void cz_mask(Regs &v, int m) {
+    constexpr auto seq = std::make_integer_sequence<int, 32>{};
+    if (m & (1 << cz_index(0, 1))) pair_neg_all<0, 1>(v, seq);
+    if (m & (1 << cz_index(0, 2))) pair_neg_all<0, 2>(v, seq);
+    if (m & (1 << cz_index(0, 3))) pair_neg_all<0, 3>(v, seq);
+    if (m & (1 << cz_index(0, 4))) pair_neg_all<0, 4>(v, seq);
+    if (m & (1 << cz_index(1, 2))) pair_neg_all<1, 2>(v, seq);
+    if (m & (1 << cz_index(1, 3))) pair_neg_all<1, 3>(v, seq);
+    if (m & (1 << cz_index(1, 4))) pair_neg_all<1, 4>(v, seq);
+    if (m & (1 << cz_index(2, 3))) pair_neg_all<2, 3>(v, seq);
+    if (m & (1 << cz_index(2, 4))) pair_neg_all<2, 4>(v, seq);
+    if (m & (1 << cz_index(3, 4))) pair_neg_all<3, 4>(v, seq);
+}
+
 // sign flip of the amplitudes whose register bits k and l are both 1 (code k | l << 3)
 __device__ __forceinline__ void pair_neg(Regs &v, int code) {
     constexpr auto seq = std::make_integer_sequence<int, 32>{};
@@ -618,6 +633,7 @@ struct OpHead {
     __device__ __forceinline__ int rval() const { return (int)(w0 >> 24); }
     __device__ __forceinline__ int count() const { return (int)(w2 >> 16); }
     __device__ __forceinline__ int first() const { return (int)(w3 & 0xffffu); }
+    __device__ __forceinline__ int czmask() const { return (int)(w1 & 0x3ffu); }   // TOP_U2L: tmask
 };
 __device__ __forceinline__ OpHead load_head(const TileOp &op) {
     const uint2 *p = reinterpret_cast<const uint2 *>(&op);
@@ -686,6 +702,7 @@ __device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ p
                     if (bits & 4) layer_gate<2>(v, pd, *lg++);
                     if (bits & 8) layer_gate<3>(v, pd, *lg++);
                     if (bits & 16) layer_gate<4>(v, pd, *lg);
+                    if (h.czmask()) cz_mask(v, h.czmask());
                     break;
                 }
                 case TOP_PAIRNEG:

@@ -263,6 +263,8 @@ constexpr int kTileMaxConds = 4;
 enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
 // TOP_U2L: a layer of uncontrolled 2x2 gates on distinct register bits (k is
 // the bit mask), in pivot form; their coefficients are lg[first...] in bit order.
+// After the gates, a CZ between register bits (k, l) for every bit set in tmask
+// (bit cz_index(k, l) over the ten pairs, see below).
 // TOP_PHASEL: a group of thread- or tile-dependent diagonal terms that all add to
 // one pending phase sum (register bit k, or the thread constant when k == 5):
 // lin[first, first + count), evaluated in place (see LinTerm); rval = 1 says that
@@ -278,6 +280,9 @@ enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
 enum TileOpKind : uint8_t {
     TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_U2L = 4, TOP_PAIR = 5, TOP_PHASEL = 6, TOP_PAIRNEG = 7
 };
+// the pairs k < l of register bits in the order (0,1) (0,2) (0,3) (0,4) (1,2)
+// (1,3) (1,4) (2,3) (2,4) (3,4): the bit of a TOP_U2L op's CZ mask
+__host__ __device__ constexpr int cz_index(int k, int l) { return k == 0 ? l - 1 : k == 1 ? l + 2 : k == 2 ? l + 4 : 9; }
 
 // A diagonal term of a TOP_PHASEL group: adds turns where the thread bits match
 // (tbits & tmask) == tval and the tile index matches (tile & fmask) == fval (its
@@ -326,8 +331,9 @@ struct TileOp {
     };
 };
 // The tile kernel reads the fields the common op kinds need (kind, k, rval,
-// count, first) as the op's first two 8-byte words, one op ahead.
+// tmask, count, first) as the op's first two 8-byte words, one op ahead.
 static_assert(offsetof(TileOp, kind) == 0 && offsetof(TileOp, k) == 1 && offsetof(TileOp, rval) == 3 &&
+                  offsetof(TileOp, tmask) == 4 &&
                   offsetof(TileOp, count) == 10 && offsetof(TileOp, first) == 12 && offsetof(TileOp, hturns) == 16,
               "TileOp head layout");
 static_assert(alignof(TileOp) >= 8, "TileOp head is read as 8-byte words");

@@ -736,6 +736,18 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
                     P.ops[w++] = o;
                 }
                 nfin = w;
+                // a CZ between register bits right after a layer op (nothing between
+                // them) becomes a bit of that op's CZ mask: one dispatch fewer
+                w = 0;
+                for (int i = 0; i < nfin; ++i) {
+                    const TileOp &o = P.ops[i];
+                    if (o.kind == TOP_PAIRNEG && w > 0 && P.ops[w - 1].kind == TOP_U2L) {
+                        P.ops[w - 1].tmask |= (uint16_t)(1u << cz_index(o.k & 7, o.k >> 3));
+                        continue;
+                    }
+                    P.ops[w++] = o;
+                }
+                nfin = w;
                 for (int q = 0; q < kTileQubits; ++q) P.fin_turns[q] = angle_turns(st.u[q]);
                 P.fin_turns[13] = angle_turns(st.u0);
                 P.fin_scale = (float)st.lam;

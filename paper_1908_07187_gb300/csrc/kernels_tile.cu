@@ -396,12 +396,13 @@ __device__ __forceinline__ void u2_bit0(Regs &v, float2 m00, float2 m01, float2 
     }
 }
 
-// amplitudes whose register bits K and L have the values of pat (bit 0: K, bit 1:
-// L) are multiplied by f
-template <int K, int L, int r>
-__device__ __forceinline__ void pair_one(Regs &v, float2 f, int pat) {
+// amplitudes whose register bits K < L have the values PAT (bit 0: K, bit 1: L)
+// are multiplied by f.  With K >= 1 the affected amplitudes fill whole float2
+// registers (register bit 0 is free), four of R and four of I: packed products.
+template <int K, int L, int PAT, int r>
+__device__ __forceinline__ void pair_one(Regs &v, float2 f) {
     constexpr int rp = ((r >> K) & 1) | (((r >> L) & 1) << 1);
-    if (pat == rp) {
+    if constexpr (rp == PAT) {
         float &x = re_of<r>(v);
         float &y = im_of<r>(v);
         const float xr = x, xi = y;
@@ -409,13 +410,34 @@ __device__ __forceinline__ void pair_one(Regs &v, float2 f, int pat) {
         y = xr * f.y + xi * f.x;
     }
 }
-template <int K, int L, int... rs>
-__device__ __forceinline__ void pair_all(Regs &v, float2 f, int pat, std::integer_sequence<int, rs...>) {
-    (pair_one<K, L, rs>(v, f, pat), ...);
+template <int K, int L, int PAT, int... rs>
+__device__ __forceinline__ void pair_all(Regs &v, float2 f, std::integer_sequence<int, rs...>) {
+    (pair_one<K, L, PAT, rs>(v, f), ...);
+}
+template <int K, int L, int PAT>
+__device__ __forceinline__ void pair_pat(Regs &v, float2 f) {
+    if constexpr (K >= 1) {
+        const float2 fr = splat(f.x), fi = splat(f.y), nfi = splat(-f.y);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int rp = ((j >> (K - 1)) & 1) | (((j >> (L - 1)) & 1) << 1);
+            if (rp != PAT) continue;
+            const float2 A = v.R[j], B = v.I[j];
+            v.R[j] = ffma2(nfi, B, __fmul2_rn(fr, A));
+            v.I[j] = ffma2(fi, A, __fmul2_rn(fr, B));
+        }
+    } else {
+        pair_all<K, L, PAT>(v, f, std::make_integer_sequence<int, 32>{});
+    }
 }
 template <int K, int L>
 __device__ __forceinline__ void pair_factor(Regs &v, float2 f, int pat) {
-    pair_all<K, L>(v, f, pat, std::make_integer_sequence<int, 32>{});
+    switch (pat) {
+        case 0: pair_pat<K, L, 0>(v, f); break;
+        case 1: pair_pat<K, L, 1>(v, f); break;
+        case 2: pair_pat<K, L, 2>(v, f); break;
+        default: pair_pat<K, L, 3>(v, f); break;
+    }
 }
 
 template <int K, int L, int r>
@@ -744,6 +766,10 @@ __device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ p
         {
             const int rb = cur == ARR_IO ? 5 : 8, wb = cur == ARR_IO ? 10 : 5;
             uint32_t t0 = pd.get0() + P.fin_turns[13];
+            for (uint64_t fm = P.fin_fixed_mask; fm; fm &= fm - 1) {
+                const int b = __ffsll((long long)fm) - 1;
+                if ((tile >> b) & 1) t0 += P.fin_fixed[b];
+            }
 #pragma unroll
             for (int j = 0; j < 5; ++j)
                 if ((lane >> j) & 1) t0 += P.fin_turns[j];

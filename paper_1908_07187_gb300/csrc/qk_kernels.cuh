@@ -355,9 +355,14 @@ struct TileHead {
     Cond conds[kTileMaxConds];
     int nops;
     // final flush: the uniform pending phase of each local qubit's |1> (turns), the
-    // uniform constant phase (fin_turns[13]) and the pass's real scale
+    // uniform constant phase (fin_turns[13]) and the real scale; a plan's last pass
+    // also applies the phases that earlier passes left on qubits outside its S:
+    // fin_fixed[b] turns where tile-index bit b (qubit fixed[b]) is 1, for the bits
+    // set in fin_fixed_mask
     uint32_t fin_turns[14];
     float fin_scale;
+    uint64_t fin_fixed_mask;
+    uint32_t fin_fixed[40];
     int fin_flip;          // local qubits stored flipped at the end (bit b: local qubit b)
     int nlg, nlin;         // entries of lg[] and lin[] in use
 };

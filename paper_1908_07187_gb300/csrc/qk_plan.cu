@@ -208,6 +208,11 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
     // kernel-parameter budget (ops and grouped phase entries)
     int max_u2 = 100, max_ph = 300;
     std::vector<POp> left, taken;
+    // the uniform pending phases one pass leaves to the next (FP64): per physical
+    // qubit, on its |1>, plus a constant phase and a real scale; only the plan's
+    // last pass applies them to the amplitudes
+    double carry[64] = {0.0};
+    double carry_u0 = 0.0, carry_lam = 1.0;
     // The gates one pass takes from rem for a qubit set S: in order, each gate
     // that commutes with every gate left behind before it, whose 2x2 target is in
     // S (with grow, a target joins S while S has room) and whose classical
@@ -653,6 +658,9 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
             // device, and what is left goes to the final flush
             {
                 UniformPending st;
+                for (int q = 0; q < kTileQubits; ++q) st.u[q] = carry[(int)P.S[q]];
+                st.u0 = carry_u0;
+                st.lam = carry_lam;
                 int arr = ARR_IO, w = 0;
                 const double pi = M_PI;
                 for (int i = 0; i < nfin; ++i) {
@@ -748,11 +756,43 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
                     P.ops[w++] = o;
                 }
                 nfin = w;
-                for (int q = 0; q < kTileQubits; ++q) P.fin_turns[q] = angle_turns(st.u[q]);
-                P.fin_turns[13] = angle_turns(st.u0);
-                P.fin_scale = (float)st.lam;
                 P.fin_flip = 0;
                 for (int q = 0; q < kTileQubits; ++q) P.fin_flip |= st.flip[q] << q;
+                P.fin_fixed_mask = 0;
+                if (left.empty()) {   // the plan's last pass applies everything pending
+                    for (int q = 0; q < kTileQubits; ++q) P.fin_turns[q] = angle_turns(st.u[q]);
+                    P.fin_turns[13] = angle_turns(st.u0);
+                    P.fin_scale = (float)st.lam;
+                    for (int b = 0; b < P.nfix; ++b) {
+                        const uint32_t t = angle_turns(carry[(int)P.fixed[b]]);
+                        P.fin_fixed[b] = t;
+                        if (t) P.fin_fixed_mask |= 1ull << b;
+                    }
+                } else {              // hand the uniform part to the next pass
+                    for (int q = 0; q < kTileQubits; ++q) {
+                        // a qubit stored flipped has its phase on |0>: e^{iu} on |0> is
+                        // e^{iu} overall times e^{-iu} on |1>
+                        const int pq = (int)P.S[q];
+                        if (st.flip[q]) {
+                            carry[pq] = -st.u[q];
+                            st.u0 += st.u[q];
+                        } else {
+                            carry[pq] = st.u[q];
+                        }
+                        P.fin_turns[q] = 0;
+                    }
+                    carry_u0 = st.u0;
+                    P.fin_turns[13] = 0;
+                    // the stored amplitudes are the true ones divided by the scale
+                    // (>= 2^-1/2 per gate): keep them within 2^24 of it in FP32
+                    if (st.lam < 0x1p-24 || st.lam > 0x1p24) {
+                        P.fin_scale = (float)st.lam;
+                        carry_lam = 1.0;
+                    } else {
+                        P.fin_scale = 1.f;
+                        carry_lam = st.lam;
+                    }
+                }
             }
             nops = nfin;
             P.nlg = nmat;

@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the one-pass-per-gate comparison")
     ap.add_argument("--no-kitaev", action="store_true", help="skip the Kitaev order-finding measurement")
+    ap.add_argument("--no-3nx1", dest="no_3nx1", action="store_true", help="skip the conventional (3nx1) order-finding run")
     ap.add_argument("--no-block", action="store_true", help="skip the dense 5-qubit block measurement")
     ap.add_argument("--no-precision", action="store_true", help="skip the complex64-vs-complex128 precision check")
     ap.add_argument("--batch-circuits", type=int, default=4096, help="circuits in the batched measurement (0: skip)")
@@ -341,6 +342,42 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def shor_3nx1_measurement(qk, torch, stream, b: int = 11, reps: int = 2):
+    """The conventional order-finding circuit (3nx1 branch of Appendix A) for a
+    seeded b-bit N: t = bit_length(N^2 - 1) control qubits and b work qubits (33
+    qubits at b = 11), H on the controls, t controlled mul-mod gathers, the work
+    register measured, the QFT sequence, the control register measured.  Device
+    time of the whole run with CUDA events, then the order and factors from the
+    control register's value by continued fractions."""
+    N, a = workloads.kitaev_parameters(b, seed=4)
+    circ = workloads.shor_3nx1_circuit(N, a, seed=3)
+    t = circ.n_qubits - N.bit_length()
+    res = {"b": b, "N": N, "a": a, "qubits": circ.n_qubits, "control_qubits": t,
+           "gate_ops": circ.gate_count(), "state_bytes": 8 << circ.n_qubits}
+    ctx = qk.Context("c64", "fused", stream=stream.cuda_stream)
+    ctx.add_qubits(circ.n_qubits)
+    ctx.add_cbits(circ.n_cbits)
+    qk.run_ops(ctx, circ.ops)            # defines the gates, allocates the gather buffer
+    ctx.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.reset()
+        qk.run_ops(ctx, circ.ops)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res["ms_per_run"] = round(e0.elapsed_time(e1) / reps, 3)
+    bits = [int(x) for x in ctx.read_cbits()]
+    ctx.close()
+    res["work_value"] = shor.register_from_bits(bits[:N.bit_length()])
+    res["y"] = shor.register_from_bits(bits[N.bit_length():])
+    r = shor.order_from_outcome(res["y"], t, a, N)
+    res["order"] = r
+    res["factors"] = shor.factors_from_order(a, r, N) if r else None
+    res["paper_context"] = "the paper runs 3nx1 for N = 8189 (39 qubits) on a desktop (Fig. 5); 39 qubits need 4 TiB of complex64, beyond one GPU"
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -850,6 +887,9 @@ def main():
                                   "controlled one, 4 per amplitude per pass (final phase and scale); lower bound"}
 
     kitaev = None
+    shor3 = None
+    if not args.no_3nx1:
+        shor3 = shor_3nx1_measurement(qk, torch, stream)
     if not args.no_kitaev:
         kitaev = kitaev_measurement(qk, torch, stream)
     block = None
@@ -892,6 +932,7 @@ def main():
             "plain_path": plain,
             "precision": precision,
             "kitaev": kitaev,
+            "shor_3nx1": shor3,
             "block5": block,
             "batched": batch,
             "serving": serving,

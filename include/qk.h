@@ -101,6 +101,7 @@ enum {
 #define QK_MAX_MATRIX_QUBITS 6
 #define QK_MAX_PERM_QUBITS 30
 #define QK_MAX_RPHASE_CBITS 62
+#define QK_MAX_MODEXP_CONTROLS 48
 
 /* Create a context with no qubits.  cuda_stream: a cudaStream_t to enqueue on
  * (borrowed, must outlive the context), or NULL for a context-owned stream.
@@ -321,6 +322,28 @@ qk_status qk_batch_apply_gates(qk_batch *b, const qk_gate_op *ops, int count);
  * errors; on an error the entries before it stay applied and qk_last_error names
  * the entry.  Lets a caller hand over a whole circuit with one call. */
 qk_status qk_apply_gates(qk_ctx *ctx, const qk_gate_op *ops, int count);
+/* Modular exponentiation of a register by a control register, as one gate: the
+ * conventional order-finding circuit (Appendix A, 3nx1 branch; Fig. 6a) applies,
+ * for c = 0 .. nCQ-1, the controlled x -> a^(2^c) x mod N on the work register
+ * under control qubit nCQ-1-c.  Those gates act on the same register and commute,
+ * so together they multiply the register value by the product of the multipliers
+ * whose control qubits are 1.  This call applies that product in one pass.
+ *   targets[0..nt)  the register, targets[0] its most significant bit;
+ *                   N <= 2^nt <= 2^QK_MAX_PERM_QUBITS
+ *   controls[j], mult[j] (j < nc <= QK_MAX_MODEXP_CONTROLS): control qubit j
+ *                   selects multiplier j (mult[j] < N, gcd(mult[j], N) = 1);
+ *                   controls distinct and not among the targets
+ *   cond_cbits[0..ncc) classical condition, as for qk_apply_gate
+ * For every basis state, the register value x < N becomes (prod over j with
+ * control j = 1 of mult[j]) x mod N; x >= N is left alone.  The result equals
+ * nc qk_apply_gate calls of qk_define_gate_perm_mulmod gates, one per (control,
+ * multiplier), in any order, and is exact.  Errors: QK_EINVAL (bad lists, N,
+ * multiplier >= N, condition), QK_ENOTBIJECTIVE (a multiplier not coprime to N),
+ * QK_ESTATE (no qubits), QK_ENOMEM (the gather buffer); the state is unchanged
+ * on an error.  Stream-ordered; one out-of-place gather, which allocates the
+ * state-sized gather buffer on first use like the permutation gates. */
+qk_status qk_apply_modexp(qk_ctx *ctx, const int *targets, int nt, const int *controls, const uint64_t *mult, int nc,
+                          uint64_t N, const int *cond_cbits, int ncc);
 qk_status qk_batch_measure(qk_batch *b, const int *qubits, int nq, const double *uniforms, const int *dest_cbits);
 qk_status qk_batch_run(qk_batch *b, int store_states);
 /* 1 when the last run has finished, 0 while it runs, -1 on error. */

@@ -245,6 +245,51 @@ __global__ void __launch_bounds__(kThreads) k_perm(const typename Amp<R>::T *__r
     }
 }
 
+// Modular exponentiation (ModExpArgs): one out-of-place gather for a whole run of
+// controlled multiplications on one register.  The group tables go to shared
+// memory once per block (their indices differ from lane to lane).
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_modexp(const typename Amp<R>::T *__restrict__ in,
+                                                     typename Amp<R>::T *__restrict__ out,
+                                                     const __grid_constant__ ModExpArgs a, const uint8_t *cbits) {
+    __shared__ uint32_t tab[kModExpGroups * 256];
+    for (int k = threadIdx.x; k < a.ngroups * 256; k += blockDim.x) tab[k] = a.tab[k >> 8][k & 255];
+    __syncthreads();
+    const bool active = (a.cond.n == 0) || cond_ok(a.cond, cbits);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_amps; i += stride) {
+        uint64_t src = i;
+        if (active) {
+            uint64_t y = 0;
+            if (a.field.contig) {
+                y = field_get(i, a.field, a.w);
+            } else {
+                for (int b = 0; b < a.w; ++b) y = (y << 1) | ((i >> a.rpos[b]) & 1u);
+            }
+            if (y < a.N) {
+                uint64_t m = 1;
+                for (int g = 0; g < a.ngroups; ++g) {
+                    uint32_t v = 0;
+                    const int j0 = 8 * g, j1 = min(a.nctl, j0 + 8);
+                    for (int j = j0; j < j1; ++j) v |= (uint32_t)((i >> a.cpos[j]) & 1u) << (j - j0);
+                    const uint64_t t = tab[(g << 8) | v];
+                    m = g == 0 ? t : mulmod_barrett(m, t, a.N, a.mu);
+                }
+                const uint64_t x = mulmod_barrett(m, y, a.N, a.mu);
+                if (a.field.contig) {
+                    src = field_put(src, x, a.field, a.w);
+                } else {
+                    for (int b = 0; b < a.w; ++b) {
+                        const uint64_t bit = (x >> (a.w - 1 - b)) & 1u;
+                        src = (src & ~(1ull << a.rpos[b])) | (bit << a.rpos[b]);
+                    }
+                }
+            }
+        }
+        out[i] = in[src];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K6: measurement.  reduce -> per-block (S0, S1); the last block to finish adds
 // the block partials in a fixed order (so results do not depend on timing) and
@@ -443,6 +488,15 @@ static cudaError_t matk_r(void *psi, const MatKArgs &a, const uint8_t *cbits, in
 cudaError_t launch_matk(int prec, void *psi, const MatKArgs &a, const uint8_t *cbits, int sms,
                         cudaStream_t s) {
     return prec == 0 ? matk_r<float>(psi, a, cbits, sms, s) : matk_r<double>(psi, a, cbits, sms, s);
+}
+
+cudaError_t launch_modexp(int prec, const void *in, void *out, const ModExpArgs &a, const uint8_t *cbits, int sms,
+                          cudaStream_t s) {
+    if (prec == 0)
+        k_modexp<float><<<grid_for(a.n_amps, sms), kThreads, 0, s>>>((const float2 *)in, (float2 *)out, a, cbits);
+    else
+        k_modexp<double><<<grid_for(a.n_amps, sms), kThreads, 0, s>>>((const double2 *)in, (double2 *)out, a, cbits);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_perm(int prec, const void *in, void *out, const PermArgs &a, const uint8_t *cbits,

@@ -825,6 +825,64 @@ qk_status qk_apply_gate(qk_ctx *c, int gate_id, const int *targets, int nt, cons
     return QK_OK;
 }
 
+qk_status qk_apply_modexp(qk_ctx *c, const int *targets, int nt, const int *controls, const uint64_t *mult, int nc,
+                          uint64_t N, const int *cond_cbits, int ncc) {
+    if (!c) return QK_EINVAL;
+    if (c->n == 0) return fail(c, QK_ESTATE, "apply_modexp: no qubits");
+    if (nt < 1 || nt > QK_MAX_PERM_QUBITS || !valid_qubits(c, targets, nt))
+        return fail(c, QK_EINVAL, "apply_modexp: bad target register");
+    if (nc < 0 || nc > QK_MAX_MODEXP_CONTROLS || !valid_qubits(c, controls, nc) || (nc > 0 && !mult))
+        return fail(c, QK_EINVAL, "apply_modexp: bad control list");
+    for (int a = 0; a < nt; ++a)
+        for (int b = 0; b < nc; ++b)
+            if (targets[a] == controls[b]) return fail(c, QK_EINVAL, "apply_modexp: qubit %d is target and control", targets[a]);
+    if (N < 2 || N > (1ull << nt)) return fail(c, QK_EINVAL, "apply_modexp: N=%llu does not fit %d qubits", (unsigned long long)N, nt);
+    qk::Cond cond{};
+    if (!fill_cond(c, cond, cond_cbits, ncc)) return fail(c, QK_EINVAL, "apply_modexp: bad classical condition");
+    std::vector<uint64_t> inv(nc);
+    for (int j = 0; j < nc; ++j) {
+        if (mult[j] >= N) return fail(c, QK_EINVAL, "apply_modexp: multiplier %d must be < N", j);
+        bool ok = false;
+        inv[j] = qk::modinv(mult[j], N, ok);
+        if (!ok)
+            return fail(c, QK_ENOTBIJECTIVE, "x -> %llu x mod %llu is not a permutation (gcd != 1)",
+                        (unsigned long long)mult[j], (unsigned long long)N);
+    }
+    if (nc == 0) return QK_OK;
+    qk_status s = flush(c);
+    if (s != QK_OK) return s;
+    s = ensure_scratch(c);
+    if (s != QK_OK) return s;
+    thread_local qk::ModExpArgs a;   // 6 KB of tables: built here, copied into the launch
+    std::memset(&a, 0, sizeof a);
+    a.w = nt;
+    for (int t = 0; t < nt; ++t) a.rpos[t] = c->l2p[targets[t]];
+    a.field = qk::reg_field_of(a.rpos, nt);
+    a.nctl = nc;
+    a.ngroups = (nc + 7) / 8;
+    for (int j = 0; j < nc; ++j) a.cpos[j] = c->l2p[controls[j]];
+    a.n_amps = 1ull << c->n;
+    a.N = N;
+    a.mu = (~0ull) / N;
+    a.cond = cond;
+    // group tables: the product of the selected inverses, exact in 64 bits (N <= 2^30)
+    for (int g = 0; g < a.ngroups; ++g) {
+        const int j0 = 8 * g, nb = std::min(8, nc - j0);
+        for (int v = 0; v < (1 << nb); ++v) {
+            uint64_t m = 1 % N;
+            for (int b = 0; b < nb; ++b)
+                if ((v >> b) & 1) m = m * inv[j0 + b] % N;
+            a.tab[g][v] = (uint32_t)m;
+        }
+    }
+    {
+        LaunchScope ls(c, 4, (double)2 * c->amp * (double)(1ull << c->n));
+        CUDA_TRY(c, qk::launch_modexp((int)c->prec, c->d_state, c->d_scratch, a, c->d_cbits, c->sms, c->stream));
+    }
+    std::swap(c->d_state, c->d_scratch);
+    return QK_OK;
+}
+
 qk_status qk_apply_gates(qk_ctx *c, const qk_gate_op *ops, int count) {
     if (!c) return QK_EINVAL;
     if (count < 0 || (count > 0 && !ops)) return fail(c, QK_EINVAL, "apply_gates: bad gate list");

@@ -103,6 +103,25 @@ struct PermArgs {
     Cond cond;
 };
 
+// Modular exponentiation of a register by a control register: for each basis
+// state, the register value x < N becomes M x mod N, M the product of the
+// multipliers whose control qubits are 1 (x >= N is left alone).  The controls go
+// in groups of 8; tab[g][v] is the inverse of the product of group g's
+// multipliers selected by the bits of v (the gather reads x = M^-1 y).
+constexpr int kModExpMaxControls = 48;
+constexpr int kModExpGroups = kModExpMaxControls / 8;
+struct ModExpArgs {
+    int w;
+    int rpos[kMaxPermW];  // physical bit of register list entry a (a = 0 is the MSB)
+    RegField field;       // zero (per-bit gather) unless set from rpos
+    int nctl, ngroups;
+    int cpos[kModExpMaxControls];   // physical bit of control j (group j / 8, bit j % 8)
+    uint64_t n_amps;
+    uint64_t N, mu;       // mu = floor((2^64-1)/N)
+    Cond cond;
+    uint32_t tab[kModExpGroups][256];
+};
+
 // Device-side record of one single-qubit measurement decision.
 struct MeasSlot {
     double p0;            // probability of reading 0
@@ -399,6 +418,8 @@ cudaError_t launch_phase(int prec, void *psi, const PhaseArgs &a, const uint8_t 
                          cudaStream_t s);
 cudaError_t launch_matk(int prec, void *psi, const MatKArgs &a, const uint8_t *cbits, int sms,
                         cudaStream_t s);
+cudaError_t launch_modexp(int prec, const void *in, void *out, const ModExpArgs &a, const uint8_t *cbits, int sms,
+                          cudaStream_t s);
 cudaError_t launch_perm(int prec, const void *in, void *out, const PermArgs &a, const uint8_t *cbits,
                         int sms, cudaStream_t s);
 cudaError_t launch_measure_reduce(int prec, const void *psi, int n, const MeasArgs &a, const MeasSlot *slots,

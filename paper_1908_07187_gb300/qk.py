@@ -129,6 +129,8 @@ _SIGS = {
     "qk_batch_stats": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                         ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "qk_apply_gates": ([_P, _P, ctypes.c_int], ctypes.c_int),
+    "qk_apply_modexp": ([_P, _IP, ctypes.c_int, _IP, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int, ctypes.c_uint64,
+                         _IP, ctypes.c_int], ctypes.c_int),
     "qk_batch_last_error": ([_P], ctypes.c_char_p),
     "qk_last_error": ([_P], ctypes.c_char_p),
     "qk_status_str": ([ctypes.c_int], ctypes.c_char_p),
@@ -262,6 +264,18 @@ class Context:
         """A whole gate list (GATE_OP_DTYPE entries) in one call."""
         arr = np.ascontiguousarray(ops, dtype=GATE_OP_DTYPE)
         self._check(_lib.qk_apply_gates(self._h, arr.ctypes.data, len(arr)))
+
+    def apply_modexp(self, targets: Sequence[int], controls: Sequence[int], multipliers: Sequence[int], N: int,
+                     cond: Sequence[int] = ()):
+        """Multiply the register (targets, first = MSB) by the product of the
+        multipliers whose control qubits are 1, mod N, in one pass."""
+        if len(controls) != len(multipliers):
+            raise ValueError("one multiplier per control")
+        t, nt = _ints(targets)
+        c, nc = _ints(controls)
+        k, nk = _ints(cond)
+        m = (ctypes.c_uint64 * max(1, len(multipliers)))(*[int(x) for x in multipliers])
+        self._check(_lib.qk_apply_modexp(self._h, t, nt, c, m, nc, int(N), k, nk))
 
     def apply_rphase_cbits(self, target: int, cbits: Sequence[int]):
         cb, n = _ints(cbits)
@@ -499,8 +513,28 @@ class Batch:
 def run_ops(ctx: Context, ops) -> None:
     """Marshal a sequence of workloads.Op into libqk calls (no arithmetic on
     amplitudes here; measurements are enqueued without waiting)."""
-    for op in ops:
+    ops = list(ops)
+    i = 0
+    while i < len(ops):
+        op = ops[i]
         k = op.kind
+        i += 1
+        if k == "mulmod" and len(op.controls) == 1 and not op.cond:
+            # a run of singly controlled multiplications on one register (they
+            # commute) goes to the library as one modular exponentiation
+            N = int(op.params[2])
+            run = [op]
+            while i < len(ops):
+                nx = ops[i]
+                if not (nx.kind == "mulmod" and len(nx.controls) == 1 and not nx.cond and nx.targets == op.targets
+                        and int(nx.params[2]) == N and nx.controls[0] not in [r.controls[0] for r in run]):
+                    break
+                run.append(nx)
+                i += 1
+            if len(run) > 1:
+                ctx.apply_modexp(op.targets, [r.controls[0] for r in run],
+                                 [pow(int(r.params[0]), 1 << int(r.params[1]), N) for r in run], N)
+                continue
         if k == "measure":
             ctx.measure(op.targets, op.uniforms, op.cbits or None, wait=False)
         elif k == "mulmod":

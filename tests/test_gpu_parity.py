@@ -184,6 +184,52 @@ def test_mulmod_on_contiguous_registers_bit_exact(qk, reg):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("reg,ctrls", [
+    ([9, 2, 4, 11, 1, 7, 12, 5], [3, 0, 6, 10, 8]),                  # scattered register and controls
+    (list(range(6, 14)), [5, 4, 3, 2, 1, 0, 14, 15, 16, 17]),       # contiguous register, 10 controls (2 groups)
+])
+def test_modexp_equals_controlled_mulmods_bit_exact(qk, prec, reg, ctrls):
+    """One modular-exponentiation call against the oracle's controlled
+    multiplications applied one after another (Appendix A, 3nx1 branch): a
+    permutation, so bit-exact; the qubit map is relabelled first (SWAPs) so that
+    the call's logical qubits sit elsewhere physically."""
+    n = 18
+    N, a = 221, 7                      # 221 = 13 * 17, gcd(7, 221) = 1
+    mults = [pow(a, 1 << j, N) for j in range(len(ctrls))]
+    psi = workloads.random_state(n, 31)
+    ctx = new_ctx(qk, n, prec, "fused", psi)
+    ctx.apply_gate("swap", [0, 13])
+    ctx.apply_gate("swap", [5, 17])
+    ctx.apply_modexp(reg, ctrls, mults, N)
+    got = ctx.get_state()
+    ref = oracle.OracleState(n, psi=psi.astype(np.complex64 if prec == "c64" else np.complex128))
+    ref.apply_matrix(oracle.gate_matrix("swap"), [0, 13])
+    ref.apply_matrix(oracle.gate_matrix("swap"), [5, 17])
+    for c, m in zip(ctrls, mults):
+        ref.apply_mulmod(m, N, reg, [c])
+    assert np.array_equal(got, ref.psi.astype(got.dtype))
+    ctx.close()
+
+
+def test_modexp_condition_and_rejections(qk):
+    n = 14
+    psi = workloads.random_state(n, 33)
+    ctx = new_ctx(qk, n, "c64", "plain", psi, ncb=2)
+    reg, ctrls = [4, 5, 6, 7, 8, 9, 10, 11], [0, 1, 2]
+    ctx.apply_modexp(reg, ctrls, [2, 4, 16], 255, cond=[1])          # cbit 1 is 0: nothing happens
+    assert np.array_equal(ctx.get_state(), psi.astype(np.complex64))
+    for args, status in [((reg, ctrls, [3, 4, 16], 255), "QK_ENOTBIJECTIVE"),   # gcd(3, 255) = 3
+                         ((reg, ctrls, [2, 4, 300], 255), "QK_EINVAL"),          # multiplier >= N
+                         ((reg, [0, 4, 2], [2, 4, 16], 255), "QK_EINVAL"),       # control among the targets
+                         ((reg, ctrls, [2, 4, 16], 257), "QK_EINVAL"),           # N > 2^8
+                         ((reg, [0, 1, 1], [2, 4, 16], 255), "QK_EINVAL")]:      # repeated control
+        with pytest.raises(qk.QKError, match=status):
+            ctx.apply_modexp(*args)
+    assert np.array_equal(ctx.get_state(), psi.astype(np.complex64))
+    ctx.close()
+
+
 def test_perm_table_and_rejections(qk):
     n = 6
     rng = np.random.default_rng(3)

@@ -11,12 +11,14 @@
 // FP32, close to full FP32 accuracy (Markidis et al., "NVIDIA Tensor Core
 // programmability, performance & precision", 2018).
 //
-// Per CTA (128 threads): a 128-row tile of X arrives by TMA (128-byte swizzle)
-// into shared memory; the threads write Xl beside it; one thread issues 24
-// tcgen05.mma (3 products x 8 K-steps of 8) into a 128 x 64 FP32 accumulator in
-// tensor memory; the four warps read their 32 rows back with tcgen05.ld and
-// store them in place.  Every mbarrier wait has an iteration limit; on timeout
-// the kernel records an error and leaves the loop, releasing its tensor memory.
+// One persistent CTA per SM, its warps specialised and pipelined: 128-row tiles
+// of X arrive by TMA (128-byte swizzle) into a three-stage shared-memory ring;
+// four warps write Xl beside each; one thread issues 24 tcgen05.mma (3 products
+// x 8 K-steps of 8) into one of two 128 x 64 FP32 accumulators in tensor memory;
+// four other warps read a finished accumulator back with tcgen05.ld and store it
+// in place while the next tile's products run.  Every mbarrier wait has an
+// iteration limit; on timeout the kernel records an error, waits (bounded) for
+// its own copies in flight, releases its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -33,10 +35,12 @@ constexpr int kChunk = kRows * 128;           // one 128-byte-wide K chunk of th
 constexpr int kTile = 2 * kChunk;             // 32 KiB
 constexpr int kBChunk = kCols * 128;          // 8 KiB
 constexpr int kB = 2 * kBChunk;               // 16 KiB
-constexpr int kThreads = 128;
-constexpr int kSmemBytes = 1024 + 2 * kTile + 2 * kB + 64;
+constexpr int kThreads = 320;                 // 10 warps: producer, MMA, 4 split, 4 epilogue
+constexpr int kStages = 3;                    // ring of X / Xl tiles
+constexpr int kSmemBytes = 1024 + 2 * kStages * kTile + 2 * kB + (3 * kStages + 4) * 8 + 16;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory per CTA");
 constexpr uint32_t kWaitLimit = 1u << 22;     // bounded mbarrier waits
-constexpr uint32_t kTmemCols = 64;
+constexpr uint32_t kTmemCols = 128;           // two 128 x 64 FP32 accumulators
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -75,6 +79,25 @@ __global__ void k_wait_selftest(int *err, uint32_t limit) {
     if (!mbar_wait(b, 0, limit)) atomicExch(err, 1);
 }
 
+// AND of v over the 128 threads of the four epilogue warps (named barrier 1), so
+// that they leave the loop together and their later barrier 1 syncs stay matched
+__device__ __forceinline__ bool epilogue_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.and.pred p, 1, 128, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+// shared -> global tile store (bulk group of the issuing thread); rows beyond the
+// tensor's extent are not written
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"((uint64_t)map),
+                 "r"(x), "r"(y), "r"(src)
+                 : "memory");
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -127,26 +150,46 @@ __device__ __forceinline__ uint32_t swz_offset(int row, int col, int rows) {
     return (uint32_t)(chunk * rows * 128 + row * 128 + ((((c >> 2) ^ (row & 7)) << 4) | ((c & 3) << 2)));
 }
 
-__global__ void __launch_bounds__(kThreads, 2)
+// Warp roles of the persistent kernel (one CTA per SM, tiles strided by the grid):
+//   warp 0        TMA producer: tile i into ring stage i % kStages
+//   warp 1        owns tensor memory; lane 0 issues the MMAs of tile i into
+//                 accumulator i % 2 once the tile's low parts are written
+//   warps 2..5    split: Xl = X - Xh for the stage
+//   warps 6..9    epilogue: accumulator -> registers -> the stage's X buffer
+//                 (same swizzled layout) -> the state, in place, by TMA store
+// Barriers (all waits bounded): full[s] (TMA bytes landed), split[s] (the four
+// split warps wrote Xl), empty[s] (the stage's result store has read it),
+// accfull[a] (accumulator a holds a finished tile), accempty[a] (the epilogue
+// read accumulator a).  Phase parities follow each barrier's use count.
+__global__ void __launch_bounds__(kThreads, 1)
     k_block_tc(float *__restrict__ psi, const __grid_constant__ CUtensorMap tmap, const float *__restrict__ bh_g,
                const float *__restrict__ bl_g, uint64_t n_groups, uint64_t n_tiles, int *err) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *sA = smem;                  // X tile as loaded (Xh: the MMA ignores the low bits)
-    unsigned char *sAl = smem + kTile;         // Xl
-    unsigned char *sBh = smem + 2 * kTile;
+    unsigned char *sA = smem;                          // kStages X tiles (the MMA reads them as Xh)
+    unsigned char *sAl = smem + kStages * kTile;       // kStages Xl tiles
+    unsigned char *sBh = smem + 2 * kStages * kTile;
     unsigned char *sBl = sBh + kB;
-    uint64_t *bars = (uint64_t *)(sBl + kB);   // [0] tile loaded, [1] MMAs done
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2);
+    uint64_t *bars = (uint64_t *)(sBl + kB);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 3 * kStages + 4);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t bar_full = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+    auto bar = [&](int k) { return smem_u32(&bars[k]); };
+    // barrier indices
+    const int FULL = 0, SPLIT = kStages, EMPTY = 2 * kStages, ACCF = 3 * kStages, ACCE = 3 * kStages + 2;
 
     if (tid == 0) {
-        mbar_init(bar_full, 1);
-        mbar_init(bar_mma, 1);
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(bar(FULL + st), 1);
+            mbar_init(bar(SPLIT + st), 4);
+            mbar_init(bar(EMPTY + st), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(bar(ACCF + a), 1);
+            mbar_init(bar(ACCE + a), 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols)
                      : "memory");
@@ -163,26 +206,64 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-
+    // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const uint64_t my_tiles = n_tiles > blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     bool ok = true;
-    uint32_t phase = 0;
-    for (uint64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, phase ^= 1u) {
-        if (tid == 0) {
-            mbar_expect_tx(bar_full, kTile);
-            tma_load_2d(smem_u32(sA), &tmap, 0, (int)(tile * kRows), bar_full);
-            tma_load_2d(smem_u32(sA + kChunk), &tmap, 32, (int)(tile * kRows), bar_full);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint64_t issued = 0;
+            for (uint64_t li = 0; li < my_tiles && ok; ++li) {
+                const int st = (int)(li % kStages);
+                const uint32_t use = (uint32_t)(li / kStages);
+                if (li >= (uint64_t)kStages && !mbar_wait(bar(EMPTY + st), (use - 1) & 1u)) { ok = false; break; }
+                const uint64_t tile = blockIdx.x + li * gridDim.x;
+                mbar_expect_tx(bar(FULL + st), kTile);
+                tma_load_2d(smem_u32(sA + st * kTile), &tmap, 0, (int)(tile * kRows), bar(FULL + st));
+                tma_load_2d(smem_u32(sA + st * kTile + kChunk), &tmap, 32, (int)(tile * kRows), bar(FULL + st));
+                ++issued;
+            }
+            // before leaving, wait (bounded) until the copies this thread issued
+            // have landed, so that none writes shared memory after the CTA ends
+            const uint64_t first = issued > (uint64_t)kStages ? issued - kStages : 0;
+            for (uint64_t li = first; li < issued; ++li)
+                if (!mbar_wait(bar(FULL + (int)(li % kStages)), (uint32_t)(li / kStages) & 1u)) ok = false;
         }
-        // every thread takes the same decision, so the barriers below stay matched
-        if (!__syncthreads_and(mbar_wait(bar_full, phase))) {
-            ok = false;
-            break;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (uint64_t li = 0; li < my_tiles && ok; ++li) {
+                const int st = (int)(li % kStages), acc = (int)(li & 1);
+                const uint32_t use = (uint32_t)(li / kStages), ause = (uint32_t)(li >> 1);
+                if (!mbar_wait(bar(SPLIT + st), use & 1u)) { ok = false; break; }
+                if (li >= 2 && !mbar_wait(bar(ACCE + acc), (ause - 1) & 1u)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned char *xa = sA + st * kTile, *xl = sAl + st * kTile;
+                const unsigned char *As[3] = {xa, xa, xl};
+                const unsigned char *Bs[3] = {sBh, sBl, sBh};
+                const uint32_t d = tmem + (uint32_t)(acc * kCols);
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const uint32_t koff = (uint32_t)((kk & 3) * 32);
+                        const uint64_t a = smem_desc(smem_u32(As[p] + (kk >> 2) * kChunk) + koff);
+                        const uint64_t b = smem_desc(smem_u32(Bs[p] + (kk >> 2) * kBChunk) + koff);
+                        mma_tf32(d, a, b, (p | kk) ? 1u : 0u);
+                    }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 bar(ACCF + acc))
+                             : "memory");
+            }
         }
-        // Xl = X - Xh, elementwise over the whole tile (same swizzled positions)
-        {
-            const float4 *src = (const float4 *)sA;
-            float4 *dst = (float4 *)sAl;
+    } else if (warp < 6) {
+        const int sid = tid - 64;                      // 0..127
+        for (uint64_t li = 0; li < my_tiles && ok; ++li) {
+            const int st = (int)(li % kStages);
+            if (!mbar_wait(bar(FULL + st), (uint32_t)(li / kStages) & 1u)) { ok = false; break; }
+            const float4 *src = (const float4 *)(sA + st * kTile);
+            float4 *dst = (float4 *)(sAl + st * kTile);
 #pragma unroll 4
-            for (int e = tid; e < kTile / 16; e += kThreads) {
+            for (int e = sid; e < kTile / 16; e += 128) {
                 const float4 x = src[e];
                 float4 l;
                 l.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u);
@@ -191,54 +272,54 @@ __global__ void __launch_bounds__(kThreads, 2)
                 l.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u);
                 dst[e] = l;
             }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(SPLIT + st)) : "memory");
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    } else {
+        const int quad = warp & 3;                     // TMEM lanes 32 quad .. 32 quad + 31
+        const int r = quad * 32 + lane;                // tile row of this thread
+        const bool leader = tid == 192;                // issues the stores (warp 6, lane 0)
+        for (uint64_t li = 0; li < my_tiles && ok; ++li) {
+            const int st = (int)(li % kStages), acc = (int)(li & 1);
+            if (!epilogue_all(mbar_wait(bar(ACCF + acc), (uint32_t)(li >> 1) & 1u))) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned char *As[3] = {sA, sA, sAl};
-            const unsigned char *Bs[3] = {sBh, sBl, sBh};
-#pragma unroll
-            for (int p = 0; p < 3; ++p)
-#pragma unroll
-                for (int kk = 0; kk < 8; ++kk) {
-                    const uint32_t koff = (uint32_t)((kk & 3) * 32);
-                    const uint64_t a = smem_desc(smem_u32(As[p] + (kk >> 2) * kChunk) + koff);
-                    const uint64_t b = smem_desc(smem_u32(Bs[p] + (kk >> 2) * kBChunk) + koff);
-                    mma_tf32(tmem, a, b, (p | kk) ? 1u : 0u);
-                }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
-                         : "memory");
-        }
-        if (!__syncthreads_and(mbar_wait(bar_mma, phase))) {
-            ok = false;
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: warp w holds rows 32w..32w+31 (TMEM lanes), 64 FP32 columns
-        {
             float v0[32], v1[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * kCols);
             tmem_ld32(taddr, v0);
             tmem_ld32(taddr + 32, v1);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            const uint64_t row = tile * kRows + (uint64_t)(warp * 32 + lane);
-            if (row < n_groups) {
-                float4 *dst = (float4 *)(psi + row * kCols);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(ACCE + acc)) : "memory");
+            // the result row into the stage's X buffer (the products have read it)
+            unsigned char *xs = sA + st * kTile;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) dst[q] = make_float4(v0[4 * q], v0[4 * q + 1], v0[4 * q + 2], v0[4 * q + 3]);
+            for (int q = 0; q < 8; ++q)
+                *(float4 *)(xs + swz_offset(r, 4 * q, kRows)) = make_float4(v0[4 * q], v0[4 * q + 1], v0[4 * q + 2], v0[4 * q + 3]);
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    dst[8 + q] = make_float4(v1[4 * q], v1[4 * q + 1], v1[4 * q + 2], v1[4 * q + 3]);
+            for (int q = 0; q < 8; ++q)
+                *(float4 *)(xs + swz_offset(r, 32 + 4 * q, kRows)) =
+                    make_float4(v1[4 * q], v1[4 * q + 1], v1[4 * q + 2], v1[4 * q + 3]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.sync 1, 128;" ::: "memory");    // the four epilogue warps
+            if (leader) {
+                const uint64_t tile = blockIdx.x + li * gridDim.x;
+                tma_store_2d(&tmap, 0, (int)(tile * kRows), smem_u32(xs));
+                tma_store_2d(&tmap, 32, (int)(tile * kRows), smem_u32(xs + kChunk));
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                // the stage goes back to the producer once the stores have read it
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar(EMPTY + st)) : "memory");
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        // every store complete before the CTA ends
+        if (leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
-    if (!ok && tid == 0) atomicExch(err, 1);
+    if (!ok) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
     }
@@ -291,7 +372,7 @@ cudaError_t launch_block_tc(void *psi, int n, const float *bh, const float *bl, 
         attr_set[dev] = true;
     }
     const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
-    uint64_t grid = n_tiles < (uint64_t)(2 * sms) ? n_tiles : (uint64_t)(2 * sms);
+    uint64_t grid = n_tiles < (uint64_t)sms ? n_tiles : (uint64_t)sms;   // persistent: one CTA per SM
     k_block_tc<<<(unsigned)grid, kThreads, kSmemBytes, s>>>((float *)psi, map, bh, bl, n_groups, n_tiles, err);
     return cudaGetLastError();
 }

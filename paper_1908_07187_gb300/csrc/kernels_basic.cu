@@ -428,6 +428,53 @@ __global__ void __launch_bounds__(kThreads) k_relabel(const typename Amp<R>::T *
     }
 }
 
+// The same permutation, tiled: a tile is every value of the output bits that
+// are the five lowest or come from the five lowest input bits (m <= 10 bits),
+// the other bits fixed.  Its 2^m amplitudes are read as runs along the input low
+// bits and written as runs along the output low bits, through shared memory.
+struct RelabelTiled {
+    int m, n_other;
+    uint64_t n_tiles;
+    int other_out[40], other_in[40];   // tile-index bit t -> output bit / input bit
+    uint64_t in_off[1024];             // input offset of tile element u (input-local order)
+    uint64_t out_off[1024];            // output offset of tile element v (output-local order)
+    uint16_t src_of[1024];             // input-local index of output-local element v
+};
+
+// Tiled relabel (RelabelTiled): persistent CTAs, offset tables in shared memory;
+// the tile buffer is XOR-swizzled on its low five index bits so that reads along
+// either side's runs stay conflict-free.
+__device__ __forceinline__ int relabel_slot(int u) { return u ^ ((u >> 5) & 31); }
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_relabel_tiled(const typename Amp<R>::T *__restrict__ in,
+                                                            typename Amp<R>::T *__restrict__ out,
+                                                            const __grid_constant__ RelabelTiled a) {
+    using T = typename Amp<R>::T;
+    __shared__ uint64_t s_in[1024], s_out[1024];
+    __shared__ uint16_t s_src[1024];
+    __shared__ T buf[1024];
+    const int M = 1 << a.m;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        s_in[k] = a.in_off[k];
+        s_out[k] = a.out_off[k];
+        s_src[k] = a.src_of[k];
+    }
+    __syncthreads();
+    for (uint64_t tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+        uint64_t bin = 0, bout = 0;
+        for (int t = 0; t < a.n_other; ++t)
+            if ((tile >> t) & 1u) {
+                bin |= 1ull << a.other_in[t];
+                bout |= 1ull << a.other_out[t];
+            }
+        for (int u = threadIdx.x; u < M; u += blockDim.x) buf[relabel_slot(u)] = in[bin + s_in[u]];
+        __syncthreads();
+        for (int v = threadIdx.x; v < M; v += blockDim.x) out[bout + s_out[v]] = buf[relabel_slot(s_src[v])];
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -538,10 +585,58 @@ cudaError_t launch_set_basis(int prec, void *psi, uint64_t index, cudaStream_t s
 
 cudaError_t launch_relabel(int prec, const void *in, void *out, const RelabelArgs &a, int sms,
                            cudaStream_t s) {
+    // tile bits: output bits 0..4 and the output bits fed by input bits 0..4
+    const int n = a.n, lo = n < 5 ? n : 5;
+    int inv[64];
+    for (int j = 0; j < n; ++j) inv[a.phys_of[j]] = j;   // input bit -> output bit
+    bool in_tile[64] = {false};
+    int out_bits[10], m = 0;
+    for (int j = 0; j < lo; ++j) { in_tile[j] = true; out_bits[m++] = j; }
+    for (int i = 0; i < lo; ++i)
+        if (!in_tile[inv[i]]) { in_tile[inv[i]] = true; out_bits[m++] = inv[i]; }
+    int in_bits[10], mi = 0;
+    bool in_used[64] = {false};
+    for (int i = 0; i < lo; ++i) { in_used[i] = true; in_bits[mi++] = i; }
+    for (int k = 0; k < m; ++k) {
+        const int i = a.phys_of[out_bits[k]];
+        if (!in_used[i]) { in_used[i] = true; in_bits[mi++] = i; }
+    }
+    if (mi != m) return cudaErrorInvalidValue;        // cannot happen for a permutation
+    static thread_local RelabelTiled t;
+    t.m = m;
+    t.n_other = 0;
+    for (int j = 0; j < n; ++j)
+        if (!in_tile[j]) {
+            t.other_out[t.n_other] = j;
+            t.other_in[t.n_other] = a.phys_of[j];
+            ++t.n_other;
+        }
+    t.n_tiles = 1ull << t.n_other;
+    int in_pos[64];                                    // input bit -> input-local position
+    for (int k = 0; k < m; ++k) in_pos[in_bits[k]] = k;
+    for (int u = 0; u < (1 << m); ++u) {
+        uint64_t off = 0;
+        for (int k = 0; k < m; ++k)
+            if ((u >> k) & 1) off |= 1ull << in_bits[k];
+        t.in_off[u] = off;
+    }
+    for (int v = 0; v < (1 << m); ++v) {
+        uint64_t off = 0;
+        int u = 0;
+        for (int k = 0; k < m; ++k)
+            if ((v >> k) & 1) {
+                off |= 1ull << out_bits[k];
+                u |= 1 << in_pos[a.phys_of[out_bits[k]]];
+            }
+        t.out_off[v] = off;
+        t.src_of[v] = (uint16_t)u;
+    }
+    const uint64_t want = (uint64_t)sms * 8;
+    const unsigned grid = (unsigned)(t.n_tiles < want ? t.n_tiles : want);
     if (prec == 0)
-        k_relabel<float><<<grid_for(a.n_amps, sms), kThreads, 0, s>>>((const float2 *)in, (float2 *)out, a);
+        k_relabel_tiled<float><<<grid, kThreads, 0, s>>>((const float2 *)in, (float2 *)out, t);
     else
-        k_relabel<double><<<grid_for(a.n_amps, sms), kThreads, 0, s>>>((const double2 *)in, (double2 *)out, a);
+        k_relabel_tiled<double><<<grid, kThreads, 0, s>>>((const double2 *)in, (double2 *)out, t);
     return cudaGetLastError();
 }
 

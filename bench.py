@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the one-pass-per-gate comparison")
     ap.add_argument("--no-kitaev", action="store_true", help="skip the Kitaev order-finding measurement")
     ap.add_argument("--no-3nx1", dest="no_3nx1", action="store_true", help="skip the conventional (3nx1) order-finding run")
+    ap.add_argument("--no-33q", dest="no_33q", action="store_true", help="skip the 33-qubit run of the layered workload")
     ap.add_argument("--no-block", action="store_true", help="skip the dense 5-qubit block measurement")
     ap.add_argument("--no-precision", action="store_true", help="skip the complex64-vs-complex128 precision check")
     ap.add_argument("--batch-circuits", type=int, default=4096, help="circuits in the batched measurement (0: skip)")
@@ -342,6 +343,44 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def layered_33q_measurement(qk, torch, stream, n: int = 33, steps: int = 2):
+    """The metric's workload at its largest configuration: the same layered
+    U3/CZ + QFT + measure-all step at 33 qubits (64 GiB of complex64), device
+    time with CUDA events over `steps` steps after one warm-up step."""
+    circ = workload(n, 2)
+    gops = gate_ops(circ)
+    meas = [op for op in circ.ops if op.kind == "measure"]
+    ctx = qk.Context("c64", "fused", stream=stream.cuda_stream, profile=True)
+    ctx.add_qubits(n)
+    ctx.add_cbits(circ.n_cbits)
+
+    def step():
+        ctx.reset()
+        qk.run_ops(ctx, gops)
+        for op in meas:
+            ctx.measure(op.targets, op.uniforms, op.cbits, wait=False)
+        ctx.flush()
+
+    step()
+    ctx.sync()
+    ctx.profile()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = ctx.profile()
+    ctx.close()
+    tile = prof.get("tile", {"launches": 0, "ms": 0.0})
+    return {"n_qubits": n, "gates_per_step": len(gops), "ms_per_step": round(ms, 3),
+            "gates_per_s": round(len(gops) / (ms / 1000.0), 1),
+            "tile_passes_per_step": tile["launches"] / steps,
+            "tile_ms_per_step": round(tile["ms"] / steps, 3),
+            "state_bytes": 8 << n}
 
 
 def shor_3nx1_measurement(qk, torch, stream, b: int = 11, reps: int = 2):
@@ -887,6 +926,9 @@ def main():
                                   "controlled one, 4 per amplitude per pass (final phase and scale); lower bound"}
 
     kitaev = None
+    big = None
+    if not args.no_33q and n < 33:
+        big = layered_33q_measurement(qk, torch, stream)
     shor3 = None
     if not args.no_3nx1:
         shor3 = shor_3nx1_measurement(qk, torch, stream)
@@ -933,6 +975,7 @@ def main():
             "precision": precision,
             "kitaev": kitaev,
             "shor_3nx1": shor3,
+            "layered_33q": big,
             "block5": block,
             "batched": batch,
             "serving": serving,

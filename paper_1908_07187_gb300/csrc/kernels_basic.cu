@@ -631,7 +631,11 @@ cudaError_t launch_relabel(int prec, const void *in, void *out, const RelabelArg
         t.out_off[v] = off;
         t.src_of[v] = (uint16_t)u;
     }
-    const uint64_t want = (uint64_t)sms * 8;
+    // each CTA copies the offset tables once: give it at least about 8 tiles
+    // (small states), at most 8 CTAs per SM (large ones)
+    uint64_t want = (uint64_t)sms * 8;
+    const uint64_t per8 = t.n_tiles / 8 > (uint64_t)sms ? t.n_tiles / 8 : (uint64_t)sms;
+    if (per8 < want) want = per8;
     const unsigned grid = (unsigned)(t.n_tiles < want ? t.n_tiles : want);
     if (prec == 0)
         k_relabel_tiled<float><<<grid, kThreads, 0, s>>>((const float2 *)in, (float2 *)out, t);

@@ -230,6 +230,27 @@ def test_modexp_condition_and_rejections(qk):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("n", [1, 3, 6, 11, 15])
+def test_qubit_map_undone_bit_exact(qk, prec, n):
+    """SWAPs only edit the logical -> physical qubit map; reading the state back
+    undoes the map with one tiled gather (tiles over the low five bits on both
+    sides).  A random chain of SWAPs against the oracle's SWAP gates: bit-exact."""
+    rng = np.random.default_rng(100 + n)
+    psi = workloads.random_state(n, 40 + n)
+    ctx = new_ctx(qk, n, prec, "fused", psi)
+    ref = oracle.OracleState(n, psi=psi.astype(np.complex64 if prec == "c64" else np.complex128))
+    for _ in range(3 * n):
+        if n < 2:
+            break
+        a, b = (int(x) for x in rng.choice(n, size=2, replace=False))
+        ctx.apply_gate("swap", [a, b])
+        ref.apply_matrix(oracle.gate_matrix("swap"), [a, b])
+    got = ctx.get_state()
+    assert np.array_equal(got, ref.psi.astype(got.dtype))
+    ctx.close()
+
+
 def test_perm_table_and_rejections(qk):
     n = 6
     rng = np.random.default_rng(3)

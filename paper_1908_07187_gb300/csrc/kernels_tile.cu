@@ -656,6 +656,7 @@ struct OpHead {
     __device__ __forceinline__ int count() const { return (int)(w2 >> 16); }
     __device__ __forceinline__ int first() const { return (int)(w3 & 0xffffu); }
     __device__ __forceinline__ int czmask() const { return (int)(w1 & 0x3ffu); }   // TOP_U2L: tmask
+    __device__ __forceinline__ int count2() const { return (int)(w3 >> 16); }
 };
 __device__ __forceinline__ OpHead load_head(const TileOp &op) {
     const uint2 *p = reinterpret_cast<const uint2 *>(&op);
@@ -696,7 +697,7 @@ __device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ p
         }
 
         // while the loads are in flight: the phase table, the classical conditions
-        fill_turn_table();
+        if (P.need_tab) fill_turn_table();
         unsigned condok = 0;
         for (int c = 0; c < P.n_conds; ++c) {
             bool ok = true;
@@ -740,6 +741,29 @@ __device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ p
                     }
                     if (acc) {
                         if (h.rval()) {  // the term's qubit is stored flipped: on bit k = 0
+                            pd.add(5, acc);
+                            pd.add(h.k(), 0u - acc);
+                        } else {
+                            pd.add(h.k(), acc);
+                        }
+                    }
+                    break;
+                }
+                case TOP_PHASEB: {
+                    const uint2 *t = reinterpret_cast<const uint2 *>(&pr.lin(0)) + h.first();
+                    const int nt = h.count(), nf = h.count2();
+                    uint32_t acc = 0, uacc = 0;
+                    for (int e = 0; e < nt; ++e) {
+                        const uint2 w = t[e];
+                        acc += (((uint32_t)tbits >> w.x) & 1u) * w.y;
+                    }
+                    for (int e = nt; e < nt + nf; ++e) {
+                        const uint2 w = t[e];
+                        uacc += ((tidx >> w.x) & 1u) * w.y;
+                    }
+                    acc += uacc;
+                    if (acc) {
+                        if (h.rval()) {
                             pd.add(5, acc);
                             pd.add(h.k(), 0u - acc);
                         } else {

@@ -296,8 +296,18 @@ enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
 // fixed-bit conditions.
 // TOP_PAIRNEG: an unconditional sign flip of the amplitudes whose register bits k
 // and l are both 1 (code k | l << 3): a CZ between two register bits.
+// TOP_PHASEB: a TOP_PHASEL group whose terms each test one bit (so every term is
+// "add turns where the bit is 1"; a term on a bit being 0 was split by the planner
+// into a constant it keeps and a negated bit-1 term): count thread-bit terms
+// followed by count2 tile-index-bit terms, BitTerm entries from index first of the
+// lin[] storage read as BitTerms (two per LinTerm slot); rval as for TOP_PHASEL.
 enum TileOpKind : uint8_t {
-    TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_U2L = 4, TOP_PAIR = 5, TOP_PHASEL = 6, TOP_PAIRNEG = 7
+    TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_PHASEB = 3, TOP_U2L = 4, TOP_PAIR = 5, TOP_PHASEL = 6,
+    TOP_PAIRNEG = 7
+};
+struct BitTerm {
+    uint32_t bit;          // thread-bit index (lane 0..4, warp 5..7) or tile-index bit
+    uint32_t turns;
 };
 // the pairs k < l of register bits in the order (0,1) (0,2) (0,3) (0,4) (1,2)
 // (1,3) (1,4) (2,3) (2,4) (3,4): the bit of a TOP_U2L op's CZ mask
@@ -350,9 +360,9 @@ struct TileOp {
     };
 };
 // The tile kernel reads the fields the common op kinds need (kind, k, rval,
-// tmask, count, first) as the op's first two 8-byte words, one op ahead.
+// tmask, count, first, count2) as the op's first two 8-byte words, one op ahead.
 static_assert(offsetof(TileOp, kind) == 0 && offsetof(TileOp, k) == 1 && offsetof(TileOp, rval) == 3 &&
-                  offsetof(TileOp, tmask) == 4 &&
+                  offsetof(TileOp, tmask) == 4 && offsetof(TileOp, count2) == 14 &&
                   offsetof(TileOp, count) == 10 && offsetof(TileOp, first) == 12 && offsetof(TileOp, hturns) == 16,
               "TileOp head layout");
 static_assert(alignof(TileOp) >= 8, "TileOp head is read as 8-byte words");
@@ -380,6 +390,7 @@ struct TileHead {
     // set in fin_fixed_mask
     uint32_t fin_turns[14];
     float fin_scale;
+    int need_tab;          // 0: every phase the pass can form is 0 or half a turn
     uint64_t fin_fixed_mask;
     uint32_t fin_fixed[40];
     int fin_flip;          // local qubits stored flipped at the end (bit b: local qubit b)

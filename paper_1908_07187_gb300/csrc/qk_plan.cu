@@ -712,11 +712,51 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
                             o.tval ^= (uint16_t)(o.tmask & tflip);
                             break;
                         }
-                        case TOP_PHASEL:
+                        case TOP_PHASEL: {
                             for (int e = o.first; e < o.first + o.count; ++e)
                                 P.lin[e].tval ^= (uint16_t)(P.lin[e].tmask & tflip);
                             o.rval = (uint8_t)(o.k < 5 ? (rflip >> o.k) & 1 : 0);
+                            // every term tests one bit: "turns where the bit is 1" terms
+                            // (TOP_PHASEB), a term on a bit being 0 split into a
+                            // constant kept here and a negated bit-1 term
+                            bool single = true;
+                            for (int e = o.first; e < o.first + o.count; ++e)
+                                single = single && __builtin_popcount(P.lin[e].tmask) + __builtin_popcount(P.lin[e].fmask) == 1;
+                            if (!single) break;
+                            std::vector<BitTerm> th, ti;
+                            uint32_t cst = 0;
+                            for (int e = o.first; e < o.first + o.count; ++e) {
+                                const LinTerm &L = P.lin[e];
+                                const bool thread = L.tmask != 0;
+                                const uint32_t b = thread ? (uint32_t)__builtin_ctz(L.tmask) : (uint32_t)__builtin_ctz(L.fmask);
+                                const uint32_t v = thread ? ((uint32_t)L.tval >> b) & 1u : (L.fval >> b) & 1u;
+                                uint32_t t = L.turns;
+                                if (!v) {
+                                    cst += t;
+                                    t = 0u - t;
+                                }
+                                (thread ? th : ti).push_back(BitTerm{b, t});
+                            }
+                            BitTerm *bt = reinterpret_cast<BitTerm *>(&P.lin[o.first]);
+                            for (size_t q = 0; q < th.size(); ++q) bt[q] = th[q];
+                            for (size_t q = 0; q < ti.size(); ++q) bt[th.size() + q] = ti[q];
+                            o.kind = TOP_PHASEB;
+                            o.first = (uint16_t)(2 * o.first);
+                            o.count = (uint16_t)th.size();
+                            o.count2 = (uint16_t)ti.size();
+                            if (cst) {   // the same for every thread and tile: kept here
+                                const double ang = turns_angle(cst);
+                                if (o.k == 5) {
+                                    st.u0 += ang;
+                                } else if (st.flip[qk_of(o.k)]) {
+                                    st.u0 += ang;
+                                    st.u[qk_of(o.k)] -= ang;
+                                } else {
+                                    st.u[qk_of(o.k)] += ang;
+                                }
+                            }
                             break;
+                        }
                         case TOP_PHASE:
                             o.rval ^= (uint8_t)(o.rmask & rflip);
                             o.tval ^= (uint16_t)(o.tmask & tflip);
@@ -797,6 +837,26 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
             nops = nfin;
             P.nlg = nmat;
             P.nlin = nlin;
+            // whether any phase factor the pass forms can be other than 1 or -1 (the
+            // kernel fills its phase table only then)
+            {
+                auto general = [](uint32_t t) { return t != 0u && t != 0x80000000u; };
+                bool need = false;
+                for (int i = 0; i < nops && !need; ++i) {
+                    const TileOp &o = P.ops[i];
+                    if (o.kind == TOP_U2 || o.kind == TOP_PHASE) need = true;
+                    if (o.kind == TOP_PHASEL)
+                        for (int e = o.first; e < o.first + o.count; ++e) need = need || general(P.lin[e].turns);
+                    if (o.kind == TOP_PHASEB) {
+                        const BitTerm *bt = reinterpret_cast<const BitTerm *>(&P.lin[0]) + o.first;
+                        for (int e = 0; e < o.count + o.count2; ++e) need = need || general(bt[e].turns);
+                    }
+                }
+                for (int q = 0; q < 14; ++q) need = need || general(P.fin_turns[q]);
+                for (int b = 0; b < P.nfix; ++b)
+                    if ((P.fin_fixed_mask >> b) & 1) need = need || general(P.fin_fixed[b]);
+                P.need_tab = need ? 1 : 0;
+            }
         }
         P.nops = nops;
         P.store_arr = cur;

@@ -97,3 +97,27 @@ def test_block_tc_on_any_qubits_matches_oracle(qk, n, blocks):
         err = float(np.max(np.abs(got - ref.psi)))
         assert err <= 1e-5, (mode, err)
         ctx.close()
+
+
+@pytest.mark.parametrize("targets", [(4, 3, 2, 1, 0), (21, 6, 13, 2, 17)])
+def test_block_tc_many_tiles_per_cta_matches_oracle(qk, targets):
+    """24 qubits: 2^19 group rows, 4096 tiles of 128 rows, about 27 per persistent
+    CTA, so every stage of the tile ring and both accumulators are reused many
+    times; two blocks in a row against the oracle."""
+    n = 24
+    rng = np.random.default_rng(2400 + targets[0])
+    U = haar(32, rng)
+    psi = workloads.random_state(n, 2401)
+    ctx = qk.Context("c64", "plain")
+    ctx.add_qubits(n)
+    ctx.set_state(psi)
+    gid = ctx.define_gate_matrix(U)
+    ctx.apply_gate(gid, list(targets))
+    ctx.apply_gate(gid, list(targets))
+    got = ctx.get_state().astype(np.complex128)
+    ctx.close()
+    ref = oracle.OracleState(n, psi=psi, openmp=True)
+    ref.apply_matrix(U, list(targets))
+    ref.apply_matrix(U, list(targets))
+    err = float(np.max(np.abs(got - ref.psi)))
+    assert err <= 1e-5, err

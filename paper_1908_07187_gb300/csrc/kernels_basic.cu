@@ -417,17 +417,6 @@ __global__ void k_set_basis(typename Amp<R>::T *psi, uint64_t index) {
     psi[index] = one;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_relabel(const typename Amp<R>::T *__restrict__ in,
-                                                      typename Amp<R>::T *__restrict__ out, RelabelArgs a) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_amps; i += stride) {
-        uint64_t p = 0;
-        for (int q = 0; q < a.n; ++q) p |= ((i >> q) & 1ull) << a.phys_of[q];
-        out[i] = in[p];
-    }
-}
-
 // The same permutation, tiled: a tile is every value of the output bits that
 // are the five lowest or come from the five lowest input bits (m <= 10 bits),
 // the other bits fixed.  Its 2^m amplitudes are read as runs along the input low

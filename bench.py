@@ -422,29 +422,34 @@ def shor_3nx1_measurement(qk, torch, stream, b: int = 11, reps: int = 2):
 # ---------------------------------------------------------------------------
 # dense 5-qubit block (secondary measurement)
 # ---------------------------------------------------------------------------
-def block_measurement(qk, torch, stream, n: int, reps: int = 10):
-    """One dense 5-qubit unitary on qubits 0..4 of an n-qubit complex64 state,
-    tensor cores (3xTF32) vs CUDA cores; device time per pass with CUDA events."""
+def block_measurement(qk, torch, stream, n: int, reps: int = 10, k: int = 5):
+    """One dense k-qubit unitary on the lowest qubits of an n-qubit complex64
+    state, tensor cores (3xTF32; k < 5 as the 5-qubit block U (x) I) vs CUDA
+    cores; device time per pass with CUDA events.  Flops count the k-qubit
+    product (2^(n-k) groups x (2^(k+1))^2 x 2)."""
     import numpy as np
 
+    d = 1 << k
     g = np.random.Generator(np.random.PCG64(5))
-    z = (g.standard_normal((32, 32)) + 1j * g.standard_normal((32, 32))) / np.sqrt(2)
+    z = (g.standard_normal((d, d)) + 1j * g.standard_normal((d, d))) / np.sqrt(2)
     q, r = np.linalg.qr(z)
     U = q * (np.diag(r) / np.abs(np.diag(r)))
-    out = {"n": n, "alg_bytes_per_pass": 2 * 8 * 2 ** n,
-           "alg_flops_per_pass": 2 ** (n - 5) * 64 * 64 * 2}
+    low = list(range(k - 1, -1, -1))
+    other = list(range(10 + k - 1, 9, -1))
+    out = {"n": n, "k": k, "alg_bytes_per_pass": 2 * 8 * 2 ** n,
+           "alg_flops_per_pass": 2 ** (n - k) * (2 * d) * (2 * d) * 2}
     for tc in (True, False):
         ctx = qk.Context("c64", "plain", stream=stream.cuda_stream, tensor_cores=tc)
         ctx.add_qubits(n)
         gid = ctx.define_gate_matrix(U)
         ctx.apply_gate("h", [0])
         for _ in range(2):
-            ctx.apply_gate(gid, [4, 3, 2, 1, 0])
+            ctx.apply_gate(gid, low)
         ctx.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            ctx.apply_gate(gid, [4, 3, 2, 1, 0])
+            ctx.apply_gate(gid, low)
         e1.record(stream)
         ctx.sync()
         ms = e0.elapsed_time(e1) / reps
@@ -452,9 +457,9 @@ def block_measurement(qk, torch, stream, n: int, reps: int = 10):
         out[key] = {"ms_per_pass": round(ms, 4), "GBps": round(out["alg_bytes_per_pass"] / ms / 1e6, 1),
                     "TFLOPs": round(out["alg_flops_per_pass"] / ms / 1e9, 2)}
         if tc:
-            # blocks alternating between qubits 0..4 and 10..14: every application
-            # first gathers its targets onto the lowest physical qubits
-            groups = ([4, 3, 2, 1, 0], [14, 13, 12, 11, 10])
+            # blocks alternating between the lowest qubits and qubits 10..: every
+            # application first gathers its targets onto the lowest physical qubits
+            groups = (low, other)
             for g in groups:
                 ctx.apply_gate(gid, g)
             ctx.sync()
@@ -934,9 +939,10 @@ def main():
         shor3 = shor_3nx1_measurement(qk, torch, stream)
     if not args.no_kitaev:
         kitaev = kitaev_measurement(qk, torch, stream)
-    block = None
+    block = block4 = None
     if not args.no_block:
         block = block_measurement(qk, torch, stream, n)
+        block4 = block_measurement(qk, torch, stream, n, k=4)
     batch = None
     if args.batch_circuits > 0 and world == 1:
         batch = batch_measurement(qk, torch, stream, args.batch_circuits)
@@ -976,6 +982,7 @@ def main():
             "kitaev": kitaev,
             "shor_3nx1": shor3,
             "layered_33q": big,
+            "block4": block4,
             "block5": block,
             "batched": batch,
             "serving": serving,

@@ -73,7 +73,7 @@ typedef struct {
     int max_pending;          /* queued ops that force a flush; 0 = default (4096)   */
     int profile;              /* 1: time every launch with CUDA events (qk_profile)  */
     size_t hbm_budget_bytes;  /* 0 = no limit beyond free device memory             */
-    int no_tensor_cores;      /* 1: dense 5-qubit blocks on CUDA cores only           */
+    int no_tensor_cores;      /* 1: dense 3..5-qubit blocks on CUDA cores only        */
     int reserved[7];          /* must be zero                                         */
 } qk_options;
 
@@ -123,13 +123,15 @@ qk_status qk_add_cbits(qk_ctx *ctx, int n, int *first_cbit_out);
 /* Define a gate "as a matrix" (Q-Kit section, command 4): k qubits (1..6), u is the
  * 2^k x 2^k matrix, row-major, interleaved (re, im) doubles, copied.  The matrix
  * must satisfy max |U^dagger U - I| <= unitarity_tol (QK_ENOTUNITARY otherwise).
- * *gate_id receives an id >= 0 valid for the life of the context.  A 5-qubit
- * complex64 gate without controls or classical condition runs on the tensor
- * cores (3xTF32 batched complex GEMM); when its targets are not the five lowest
- * physical qubits, one relabelling pass first moves them there (the qubit map
- * records the move, no extra memory beyond the context's gather buffer).  Other
- * dense gates run on CUDA cores.  qk_sync reports QK_ETIMEOUT if a tensor-core
- * pass hit its bounded wait. */
+ * *gate_id receives an id >= 0 valid for the life of the context.  A 3-, 4- or
+ * 5-qubit complex64 gate without controls or classical condition, on a state of
+ * at least 5 qubits, runs on the tensor cores (3xTF32 batched complex GEMM; a
+ * 3- or 4-qubit gate as the 5-qubit block U (x) I with the other lowest physical
+ * qubits); when its targets are not among the lowest physical qubits, one
+ * relabelling pass first moves them there (the qubit map records the move, no
+ * extra memory beyond the context's gather buffer).  Other dense gates run on
+ * CUDA cores in the working precision.  qk_sync reports QK_ETIMEOUT if a
+ * tensor-core pass hit its bounded wait. */
 qk_status qk_define_gate_matrix(qk_ctx *ctx, int k, const double *u, double unitarity_tol, int *gate_id);
 
 /* Define a gate "as a function" (Q-Kit section, command 4; QuModExpUaj of

@@ -404,24 +404,32 @@ qk_status move_to_low(qk_ctx *c, const int *targets, int k) {
 // Dense 5-qubit gate on physical qubits 0..4 via the tensor-core kernel.  The
 // real embedding of U, with rows and columns permuted to the physical order of
 // the targets, is split into TF32 high and low parts once per target order.
+// A k-qubit gate (k = 3, 4) is the 5-qubit block U (x) I on its targets and the
+// other low physical qubits: entries whose spectator bits differ are zero.
 qk_status apply_block_tc(qk_ctx *c, int gate_id, const int *targets, uint32_t key) {
     GateDef &g = c->gates[gate_id];
+    const int k = g.k;
     float *dev = nullptr;
     for (auto &e : g.tc_cache)
         if (e.first == key) dev = e.second;
     if (!dev) {
         if (c->capturing) return fail(c, QK_ESTATE, "tensor-core matrices would be allocated during capture");
         int pa[5];
-        for (int a = 0; a < 5; ++a) pa[a] = c->l2p[targets[a]];
+        int tmask = 0;
+        for (int a = 0; a < k; ++a) {
+            pa[a] = c->l2p[targets[a]];
+            tmask |= 1 << pa[a];
+        }
         auto value = [&](int x) {  // gate register value of physical low-bit index x
             int v = 0;
-            for (int a = 0; a < 5; ++a) v |= ((x >> pa[a]) & 1) << (4 - a);
+            for (int a = 0; a < k; ++a) v |= ((x >> pa[a]) & 1) << (k - 1 - a);
             return v;
         };
+        const size_t d = (size_t)1 << k;
         std::vector<float> bh(64 * 64), bl(64 * 64);
         for (int r = 0; r < 32; ++r)
             for (int x = 0; x < 32; ++x) {
-                const cd u = g.m[(size_t)value(r) * 32 + value(x)];
+                const cd u = ((r & ~tmask) == (x & ~tmask)) ? g.m[(size_t)value(r) * d + value(x)] : cd(0.0);
                 const float re = (float)u.real(), im = (float)u.imag();
                 const float vals[4] = {re, -im, im, re};          // (2r,2x) (2r,2x+1) (2r+1,2x) (2r+1,2x+1)
                 const int idx[4] = {(2 * r) * 64 + 2 * x, (2 * r) * 64 + 2 * x + 1, (2 * r + 1) * 64 + 2 * x,
@@ -774,13 +782,15 @@ qk_status qk_apply_gate(qk_ctx *c, int gate_id, const int *targets, int nt, cons
         }
         qk_status s = flush(c);
         if (s != QK_OK) return s;
-        if (g.k == 5 && c->prec == QK_C64 && nc == 0 && ncc == 0 && !c->opt.no_tensor_cores) {
-            // targets elsewhere are first gathered onto physical qubits 0..4 (one
-            // relabelling pass), which costs far less than a CUDA-core block pass
-            qk_status sm = move_to_low(c, targets, 5);
+        if (g.k >= 3 && g.k <= 5 && c->n >= 5 && c->prec == QK_C64 && nc == 0 && ncc == 0 &&
+            !c->opt.no_tensor_cores) {
+            // targets elsewhere are first gathered onto the lowest physical qubits
+            // (one relabelling pass), which costs far less than a CUDA-core block
+            // pass; 3- and 4-qubit gates run as 5-qubit blocks U (x) I
+            qk_status sm = move_to_low(c, targets, g.k);
             if (sm != QK_OK) return sm;
             uint32_t key = 0;
-            for (int a = 0; a < 5; ++a) key |= (uint32_t)c->l2p[targets[a]] << (3 * a);
+            for (int a = 0; a < g.k; ++a) key |= (uint32_t)c->l2p[targets[a]] << (3 * a);
             return apply_block_tc(c, gate_id, targets, key);
         }
         qk::MatKArgs a{};

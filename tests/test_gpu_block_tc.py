@@ -121,3 +121,33 @@ def test_block_tc_many_tiles_per_cta_matches_oracle(qk, targets):
     ref.apply_matrix(U, list(targets))
     err = float(np.max(np.abs(got - ref.psi)))
     assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("n,targets", [(5, (2, 0, 4, 1)), (12, (4, 3, 2, 1)), (13, (9, 2, 11)), (17, (16, 3, 8, 12)),
+                                       (20, (0, 1, 2))])
+def test_three_and_four_qubit_blocks_on_tensor_cores(qk, n, targets):
+    """3- and 4-qubit dense gates run as 5-qubit tensor-core blocks U (x) I (the
+    spectator low qubits untouched), after a relabelling pass when their targets
+    are not low; against the oracle and against the CUDA-core path."""
+    k = len(targets)
+    rng = np.random.default_rng(50 * n + k)
+    U = haar(1 << k, rng)
+    psi = workloads.random_state(n, 900 + n)
+    got = {}
+    for tc in (True, False):
+        ctx = qk.Context("c64", "plain", tensor_cores=tc)
+        ctx.add_qubits(n)
+        ctx.set_state(psi)
+        gid = ctx.define_gate_matrix(U)
+        ctx.apply_gate(gid, list(targets))
+        ctx.apply_gate("h", [targets[0]])
+        ctx.apply_gate(gid, list(targets))
+        got[tc] = ctx.get_state().astype(np.complex128)
+        ctx.close()
+    ref = oracle.OracleState(n, psi=psi)
+    ref.apply_matrix(U, list(targets))
+    ref.apply_matrix(oracle.GATES_1Q["h"], [targets[0]])
+    ref.apply_matrix(U, list(targets))
+    for tc in (True, False):
+        err = float(np.max(np.abs(got[tc] - ref.psi)))
+        assert err <= 1e-5, (tc, err)

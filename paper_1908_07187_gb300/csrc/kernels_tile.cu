@@ -483,6 +483,22 @@ __device__ __forceinline__ void pair_neg(Regs &v, int code) {
     }
 }
 
+// pair factor on register bits (code k | l << 3), pattern pat of the two bits
+__device__ __forceinline__ void pair_dispatch(Regs &v, int code, float2 f, int pat) {
+    switch (code) {
+        case 0 | (1 << 3): pair_factor<0, 1>(v, f, pat); break;
+        case 0 | (2 << 3): pair_factor<0, 2>(v, f, pat); break;
+        case 0 | (3 << 3): pair_factor<0, 3>(v, f, pat); break;
+        case 0 | (4 << 3): pair_factor<0, 4>(v, f, pat); break;
+        case 1 | (2 << 3): pair_factor<1, 2>(v, f, pat); break;
+        case 1 | (3 << 3): pair_factor<1, 3>(v, f, pat); break;
+        case 1 | (4 << 3): pair_factor<1, 4>(v, f, pat); break;
+        case 2 | (3 << 3): pair_factor<2, 3>(v, f, pat); break;
+        case 2 | (4 << 3): pair_factor<2, 4>(v, f, pat); break;
+        default: pair_factor<3, 4>(v, f, pat); break;
+    }
+}
+
 template <typename Off>
 __device__ __forceinline__ bool op_applies(const TileOp &op, int tbits, Off base, unsigned condok) {
     if ((tbits & op.tmask) != op.tval) return false;
@@ -550,20 +566,7 @@ __device__ __forceinline__ void general_op(Regs &v, DevPending &pd, const TileOp
     if (op.kind == TOP_U2) pd.add(op.k, op.hturns);  // uniform part, in every thread
     if (!op_applies<Off>(op, tbits, base, condok)) return;
     if (op.kind == TOP_PAIR) {
-        const float2 f = make_float2(op.ph.re, op.ph.im);
-        const int pat = op.rval;   // values of the pair's bits (bit 0: k, bit 1: l)
-        switch (op.k) {
-            case 0 | (1 << 3): pair_factor<0, 1>(v, f, pat); break;
-            case 0 | (2 << 3): pair_factor<0, 2>(v, f, pat); break;
-            case 0 | (3 << 3): pair_factor<0, 3>(v, f, pat); break;
-            case 0 | (4 << 3): pair_factor<0, 4>(v, f, pat); break;
-            case 1 | (2 << 3): pair_factor<1, 2>(v, f, pat); break;
-            case 1 | (3 << 3): pair_factor<1, 3>(v, f, pat); break;
-            case 1 | (4 << 3): pair_factor<1, 4>(v, f, pat); break;
-            case 2 | (3 << 3): pair_factor<2, 3>(v, f, pat); break;
-            case 2 | (4 << 3): pair_factor<2, 4>(v, f, pat); break;
-            default: pair_factor<3, 4>(v, f, pat); break;
-        }
+        pair_dispatch(v, op.k, make_float2(op.ph.re, op.ph.im), op.rval);
         return;
     }
     if (op.kind == TOP_U2) {
@@ -770,6 +773,11 @@ __device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ p
                             pd.add(h.k(), acc);
                         }
                     }
+                    break;
+                }
+                case TOP_PAIRU: {
+                    const float2 f = *reinterpret_cast<const float2 *>(&pr.op(i).ph.re);
+                    pair_dispatch(v, h.k(), f, h.rval());
                     break;
                 }
                 case TOP_XPOSE:

@@ -301,9 +301,11 @@ enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
 // into a constant it keeps and a negated bit-1 term): count thread-bit terms
 // followed by count2 tile-index-bit terms, BitTerm entries from index first of the
 // lin[] storage read as BitTerms (two per LinTerm slot); rval as for TOP_PHASEL.
+// TOP_PAIRU: a TOP_PAIR without thread, tile or classical condition (the common
+// case: a controlled phase between two register bits).
 enum TileOpKind : uint8_t {
     TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_PHASEB = 3, TOP_U2L = 4, TOP_PAIR = 5, TOP_PHASEL = 6,
-    TOP_PAIRNEG = 7
+    TOP_PAIRNEG = 7, TOP_PAIRU = 8
 };
 struct BitTerm {
     uint32_t bit;          // thread-bit index (lane 0..4, warp 5..7) or tile-index bit

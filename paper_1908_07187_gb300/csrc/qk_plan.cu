@@ -710,6 +710,7 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
                             const int ka = o.k & 7, kb = o.k >> 3;
                             o.rval = (uint8_t)(3 ^ (((rflip >> ka) & 1) | (((rflip >> kb) & 1) << 1)));
                             o.tval ^= (uint16_t)(o.tmask & tflip);
+                            if (o.tmask == 0 && o.gmask == 0 && o.cond == 0xffff) o.kind = TOP_PAIRU;
                             break;
                         }
                         case TOP_PHASEL: {

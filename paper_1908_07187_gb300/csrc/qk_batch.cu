@@ -533,8 +533,14 @@ qk_status run_large(qk_batch *b) {
     b->large_launches = 0;
     for (int k = 0; k < maxp; ++k) {
         const int np = (int)((k + 1 < maxp ? launch[k + 1].first : progs.size()) - launch[k].first);
+        // the kernel instance without the general-op path when no program needs it
+        bool general = false;
+        for (int q = 0; q < np && !general; ++q) {
+            const qk::TileProg &h = progs[launch[k].first + q];
+            general = qk::tile_ops_need_general(ops.data() + h.op0, (size_t)h.nops);
+        }
         const cudaError_t e = qk::launch_tile_batch(b->d_lprogs + launch[k].first, b->d_lfirst + launch[k].second, np,
-                                                    ctas[k], b->d_lops, b->d_llg, b->d_llin, b->sms, b->stream);
+                                                    ctas[k], b->d_lops, b->d_llg, b->d_llin, general, b->stream);
         if (e != cudaSuccess) return bfail(b, QK_ECUDA, "batch: tile launch failed: %s", cudaGetErrorString(e));
         ++b->large_launches;
     }

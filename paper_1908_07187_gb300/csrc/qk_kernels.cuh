@@ -302,7 +302,9 @@ enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
 // followed by count2 tile-index-bit terms, BitTerm entries from index first of the
 // lin[] storage read as BitTerms (two per LinTerm slot); rval as for TOP_PHASEL.
 // TOP_PAIRU: a TOP_PAIR without thread, tile or classical condition (the common
-// case: a controlled phase between two register bits).
+// case: a controlled phase between two register bits), always on the stored
+// pattern (1, 1): for qubits stored flipped the planner rewrites the factor as a
+// (1, 1) factor and uniform single-bit and constant phases.
 enum TileOpKind : uint8_t {
     TOP_U2 = 0, TOP_PHASE = 1, TOP_XPOSE = 2, TOP_PHASEB = 3, TOP_U2L = 4, TOP_PAIR = 5, TOP_PHASEL = 6,
     TOP_PAIRNEG = 7, TOP_PAIRU = 8
@@ -419,8 +421,13 @@ cudaError_t launch_tile(void *psi, const TileParams &p, const uint8_t *cbits, cu
 // program c, where first[] (n_progs + 1 entries, ascending, first[0] = 0) splits
 // the grid; programs are in n-qubit order so that the 32-bit offset kernel serves
 // every circuit below 33 qubits.
+// general: some program holds general ops (see tile_ops_need_general); without
+// them a leaner instance of the kernel runs.
 cudaError_t launch_tile_batch(const TileProg *progs, const uint32_t *first, int n_progs, uint32_t n_ctas,
-                              const TileOp *ops, const LayerGate *lg, const LinTerm *lin, int sms, cudaStream_t s);
+                              const TileOp *ops, const LayerGate *lg, const LinTerm *lin, bool general,
+                              cudaStream_t s);
+// whether a pass program holds ops of the kinds TOP_U2, TOP_PHASE or TOP_PAIR
+bool tile_ops_need_general(const TileOp *ops, size_t n);
 
 // ---------------------------------------------------------------------------
 // launchers (kernels_basic.cu); prec: 0 = complex64, 1 = complex128

@@ -708,9 +708,27 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
                         }
                         case TOP_PAIR: {
                             const int ka = o.k & 7, kb = o.k >> 3;
-                            o.rval = (uint8_t)(3 ^ (((rflip >> ka) & 1) | (((rflip >> kb) & 1) << 1)));
+                            const int fa = (rflip >> ka) & 1, fb = (rflip >> kb) & 1;
                             o.tval ^= (uint16_t)(o.tmask & tflip);
-                            if (o.tmask == 0 && o.gmask == 0 && o.cond == 0xffff) o.kind = TOP_PAIRU;
+                            if (o.tmask == 0 && o.gmask == 0 && o.cond == 0xffff) {
+                                // e^{i th} where the true bits a = sa ^ fa, b = sb ^ fb are both
+                                // 1, in stored bits: (sa ^ fa)(sb ^ fb) = fa fb + fa (1 - 2 fb) sb
+                                // + fb (1 - 2 fa) sa + (1 - 2 fa)(1 - 2 fb) sa sb.  The stored
+                                // pattern (1, 1) takes +-th on the device; the constant and the
+                                // single-bit parts are uniform phases kept here.
+                                const double th = turns_angle(o.ph.turns);
+                                if (fa && fb) st.u0 += th;
+                                if (fa) st.u[qk_of(kb)] += fb ? -th : th;
+                                if (fb) st.u[qk_of(ka)] += fa ? -th : th;
+                                if (fa ^ fb) {
+                                    o.ph.turns = 0u - o.ph.turns;
+                                    o.ph.im = -o.ph.im;
+                                }
+                                o.rval = 3;
+                                o.kind = TOP_PAIRU;
+                            } else {
+                                o.rval = (uint8_t)(3 ^ (fa | (fb << 1)));
+                            }
                             break;
                         }
                         case TOP_PHASEL: {

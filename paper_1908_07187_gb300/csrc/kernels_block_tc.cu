@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "qk_kernels.cuh"
 
 namespace qk {
@@ -360,16 +362,17 @@ cudaError_t launch_block_tc(void *psi, int n, const float *bh, const float *bl, 
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
         CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    // the shared-memory attribute is set once per device
-    static bool attr_set[64] = {false};
+    // the shared-memory attribute is set once per device (host threads may launch
+    // concurrently; setting it twice is harmless)
+    static std::atomic<bool> attr_set[64];
     int dev = 0;
     cudaError_t ed = cudaGetDevice(&dev);
     if (ed != cudaSuccess) return ed;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_set[dev]) {
+    if (!attr_set[dev].load(std::memory_order_acquire)) {
         cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
         if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
+        attr_set[dev].store(true, std::memory_order_release);
     }
     const uint64_t n_tiles = (n_groups + kRows - 1) / kRows;
     uint64_t grid = n_tiles < (uint64_t)sms ? n_tiles : (uint64_t)sms;   // persistent: one CTA per SM

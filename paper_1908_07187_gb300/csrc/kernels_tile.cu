@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <utility>
 
 #include "qk_kernels.cuh"
@@ -891,17 +892,18 @@ __global__ void __launch_bounds__(kTileThreads, 2)
 // transposes (2^13 complex64) and pending sums (6 words per thread)
 constexpr int kTileSmem = ((int)(2 * sizeof(float)) << kTileQubits) + 6 * kTileThreads * 4;
 
-// the dynamic shared-memory attribute of kernel f, set once per device
+// the dynamic shared-memory attribute of kernel f, set once per device (host
+// threads of the serving loop may launch concurrently; setting it twice is harmless)
 template <typename F>
-cudaError_t tile_smem_attr(F *f, bool (&set)[64]) {
+cudaError_t tile_smem_attr(F *f, std::atomic<bool> (&set)[64]) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!set[dev]) {
+    if (!set[dev].load(std::memory_order_acquire)) {
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileSmem);
         if (e != cudaSuccess) return e;
-        set[dev] = true;
+        set[dev].store(true, std::memory_order_release);
     }
     return cudaSuccess;
 }
@@ -915,7 +917,7 @@ bool needs_general(const TileOp *ops, size_t n) {
 
 template <typename Off, bool GEN>
 cudaError_t launch_tile_g(void *psi, const TileParams &p, const uint8_t *cbits, cudaStream_t s) {
-    static bool attr_set[64] = {false};
+    static std::atomic<bool> attr_set[64];
     const cudaError_t e = tile_smem_attr(k_tile<Off, GEN>, attr_set);
     if (e != cudaSuccess) return e;
     k_tile<Off, GEN><<<(unsigned)p.n_tiles, kTileThreads, kTileSmem, s>>>((float2 *)psi, p, cbits);
@@ -933,7 +935,7 @@ cudaError_t launch_tile_t(void *psi, const TileParams &p, const uint8_t *cbits, 
 template <bool GEN>
 cudaError_t launch_tile_batch_g(const TileProg *progs, const uint32_t *first, int n_progs, uint32_t n_ctas,
                                 const TileOp *ops, const LayerGate *lg, const LinTerm *lin, cudaStream_t s) {
-    static bool attr_set[64] = {false};
+    static std::atomic<bool> attr_set[64];
     const cudaError_t e = tile_smem_attr(k_tile_batch<GEN>, attr_set);
     if (e != cudaSuccess) return e;
     k_tile_batch<GEN><<<n_ctas, kTileThreads, kTileSmem, s>>>(progs, first, n_progs, ops, lg, lin);

@@ -328,7 +328,9 @@ struct qk_batch {
     struct Large {
         int circ;                      // index in circs
         int n;
-        std::vector<qk::FusedOp> ops;  // physical qubit = qubit (no relabelling)
+        // its gates as validated list entries (physical qubit = qubit, no
+        // relabelling); the planning threads turn them into planner ops
+        std::vector<qk_gate_op> gates;
         uint64_t state_off = 0;        // in the large-state pool, amplitudes
         int npasses = 0;
     };
@@ -405,6 +407,36 @@ bool distinct(const int *q, int k, int n) {
     return true;
 }
 
+// A validated gate of a circuit above 13 qubits (one target, at most one control,
+// no classical condition) as planner ops: a 2x2 op, or one phase op per diagonal
+// entry that is not 1.
+void append_fused(std::vector<qk::FusedOp> &out, const qk_gate_op &g) {
+    qk::cd m[4];
+    int ntg = 0;
+    qk::builtin_matrix(g.gate_id, g.params, g.np, m, ntg);
+    const uint64_t cmask = g.nc ? 1ull << g.controls[0] : 0ull;
+    const int q = g.target;
+    if (m[1] == 0.0 && m[2] == 0.0) {
+        for (int e = 0; e < 2; ++e) {
+            const qk::cd f = e ? m[3] : m[0];
+            if (f == 1.0) continue;
+            qk::FusedOp o;
+            o.kind = qk::FusedOp::PHASE;
+            o.mask = cmask | (1ull << q);
+            o.val = cmask | (e ? (1ull << q) : 0ull);
+            o.f = f;
+            out.push_back(o);
+        }
+    } else {
+        qk::FusedOp o;
+        o.kind = qk::FusedOp::U2;
+        o.q = q;
+        o.cmask = cmask;
+        for (int e = 0; e < 4; ++e) o.m[e] = m[e];
+        out.push_back(o);
+    }
+}
+
 // The circuits above 13 qubits: plan each into tile passes (host threads), pack
 // the pass programs into device pools ordered by pass index, set the states to
 // |0...0> and launch pass k of every circuit that has one in one batched launch.
@@ -424,11 +456,15 @@ qk_status run_large(qk_batch *b) {
     std::atomic<int> next(0);
     auto worker = [&]() {
         qk::TilePlanner *pl = qk::make_planner();
+        std::vector<qk::FusedOp> fops;
         for (;;) {
             const int i = next.fetch_add(1);
             if (i >= nl) break;
             const auto &L = b->large[i];
             Plan &out = plans[i];
+            fops.clear();
+            fops.reserve(L.gates.size());
+            for (const qk_gate_op &g : L.gates) append_fused(fops, g);
             const qk::PassSink sink = [&](qk::TileParams &P) -> qk_status {
                 if (P.n_conds > 0) {   // unreachable: large circuits take no classical conditions
                     out.err = "batch: classical conditions are not batched above 13 qubits";
@@ -446,7 +482,7 @@ qk_status run_large(qk_batch *b) {
                 return QK_OK;
             };
             const char *err = "";
-            out.st = qk::plan_passes(pl, L.n, L.ops, sink, &err);
+            out.st = qk::plan_passes(pl, L.n, fops, sink, &err);
             if (out.st != QK_OK && out.err.empty()) out.err = err;
         }
         qk::free_planner(pl);
@@ -654,9 +690,8 @@ qk_status qk_batch_apply_gate(qk_batch *b, int gate_id, const int *targets, int 
     qk::BCirc *c;
     if (!cur_circuit(b, &c)) return bfail(b, QK_ESTATE, "batch: add a circuit first");
     const int n = (int)c->n;
-    qk::cd m[4];
     int ntg = 0;
-    if (!qk::builtin_matrix(gate_id, params, np, m, ntg) || nt != ntg || ntg != 1)
+    if (!qk::builtin_arity(gate_id, params, np, ntg) || nt != ntg || ntg != 1)
         return bfail(b, QK_EINVAL, "batch: gate %d is not a 1-target built-in with these params", gate_id);
     if (!distinct(targets, nt, n) || nc < 0 || nc > 16 || (nc > 0 && !distinct(controls, nc, n)))
         return bfail(b, QK_EINVAL, "batch: bad qubit lists");
@@ -670,28 +705,20 @@ qk_status qk_batch_apply_gate(qk_batch *b, int gate_id, const int *targets, int 
         if (ncc != 0 || nc > 1)
             return bfail(b, QK_EINVAL, "batch: circuits above %d qubits take gates with at most one control and no "
                                        "classical condition", qk::kBMaxQubits);
-        auto &L = b->large[b->large_of.back()];
-        if (m[1] == 0.0 && m[2] == 0.0) {  // diagonal: one phase op per entry that is not 1
-            for (int e = 0; e < 2; ++e) {
-                const qk::cd f = e ? m[3] : m[0];
-                if (f == 1.0) continue;
-                qk::FusedOp o;
-                o.kind = qk::FusedOp::PHASE;
-                o.mask = (uint64_t)cmask | (1ull << q);
-                o.val = (uint64_t)cmask | (e ? (1ull << q) : 0ull);
-                o.f = f;
-                L.ops.push_back(o);
-            }
-        } else {
-            qk::FusedOp o;
-            o.kind = qk::FusedOp::U2;
-            o.q = q;
-            o.cmask = cmask;
-            for (int e = 0; e < 4; ++e) o.m[e] = m[e];
-            L.ops.push_back(o);
-        }
+        // kept as a list entry; the planning threads form its matrix (append_fused)
+        qk_gate_op g;
+        std::memset(&g, 0, sizeof g);
+        g.gate_id = gate_id;
+        g.target = q;
+        g.nc = nc;
+        if (nc) g.controls[0] = controls[0];
+        g.np = np;
+        for (int k = 0; k < np; ++k) g.params[k] = params[k];
+        b->large[b->large_of.back()].gates.push_back(g);
         return QK_OK;
     }
+    qk::cd m[4];
+    qk::builtin_matrix(gate_id, params, np, m, ntg);   // valid: checked above
     qk::BOp op;
     std::memset(&op, 0, sizeof op);
     if (!fill_cond(op, *c, cond_cbits, ncc)) return bfail(b, QK_EINVAL, "batch: bad classical condition");
@@ -724,6 +751,10 @@ qk_status qk_batch_apply_gate(qk_batch *b, int gate_id, const int *targets, int 
 qk_status qk_batch_apply_gates(qk_batch *b, const qk_gate_op *ops, int count) {
     if (!b) return QK_EINVAL;
     if (count < 0 || (count > 0 && !ops)) return bfail(b, QK_EINVAL, "batch: bad gate list");
+    if (!b->large_of.empty() && b->large_of.back() >= 0) {
+        auto &G = b->large[b->large_of.back()].gates;
+        G.reserve(G.size() + (size_t)count);
+    }
     for (int i = 0; i < count; ++i) {
         const qk_gate_op &g = ops[i];
         if (g.nc < 0 || g.nc > 4 || g.ncc < 0 || g.ncc > 4 || g.np < 0 || g.np > 3)

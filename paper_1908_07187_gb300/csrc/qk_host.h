@@ -14,6 +14,20 @@ using cd = std::complex<double>;
 // ---------------------------------------------------------------------------
 // built-in gate matrices (textbook definitions; FP64)
 // ---------------------------------------------------------------------------
+// whether (id, p, np) names a built-in gate, and its target count, without
+// forming the matrix (the same cases as builtin_matrix below)
+inline bool builtin_arity(int id, const double *p, int np, int &ntargets) {
+    ntargets = 1;
+    switch (id) {
+        case QK_GATE_X: case QK_GATE_Y: case QK_GATE_Z: case QK_GATE_H:
+        case QK_GATE_S: case QK_GATE_SDG: case QK_GATE_T: case QK_GATE_TDG: return np == 0;
+        case QK_GATE_U3: return np == 3 && p;
+        case QK_GATE_P: case QK_GATE_RZ: return np == 1 && p;
+        case QK_GATE_SWAP: ntargets = 2; return np == 0;
+        default: return false;
+    }
+}
+
 inline bool builtin_matrix(int id, const double *p, int np, cd m[4], int &ntargets) {
     const double r2 = 1.0 / std::sqrt(2.0);
     const cd I(0, 1);

@@ -930,33 +930,44 @@ def main():
                          "count": "10 per amplitude pair per uncontrolled non-diagonal gate, 16 per acting pair per "
                                   "controlled one, 4 per amplitude per pass (final phase and scale); lower bound"}
 
+    # secondary measurements: a failure in one is recorded under its key and
+    # the line is still printed
+    def guarded(name, fn, *a, **kw):
+        try:
+            return fn(*a, **kw)
+        except Exception as e:  # noqa: BLE001
+            print(f"bench: {name} failed: {type(e).__name__}: {e}", file=sys.stderr)
+            return {"error": f"{type(e).__name__}: {str(e)[:300]}"}
+
     kitaev = None
     big = None
     if not args.no_33q and n < 33:
-        big = layered_33q_measurement(qk, torch, stream)
+        big = guarded("layered_33q", layered_33q_measurement, qk, torch, stream)
     shor3 = None
     if not args.no_3nx1:
-        shor3 = shor_3nx1_measurement(qk, torch, stream)
+        shor3 = guarded("shor_3nx1", shor_3nx1_measurement, qk, torch, stream)
     if not args.no_kitaev:
-        kitaev = kitaev_measurement(qk, torch, stream)
+        kitaev = guarded("kitaev", kitaev_measurement, qk, torch, stream)
     block = block4 = None
     if not args.no_block:
-        block = block_measurement(qk, torch, stream, n)
-        block4 = block_measurement(qk, torch, stream, n, k=4)
+        block = guarded("block5", block_measurement, qk, torch, stream, n)
+        block4 = guarded("block4", block_measurement, qk, torch, stream, n, k=4)
     batch = None
     if args.batch_circuits > 0 and world == 1:
-        batch = batch_measurement(qk, torch, stream, args.batch_circuits)
-        batch["dense_blocks_vs_tile"] = dense_block_measurement(qk, torch, stream)
+        batch = guarded("batched", batch_measurement, qk, torch, stream, args.batch_circuits)
+        if "error" not in batch:
+            batch["dense_blocks_vs_tile"] = guarded("dense_blocks_vs_tile", dense_block_measurement, qk, torch,
+                                                    stream)
     precision = None
     if not args.no_precision and args.mode == "fused":
-        precision = precision_measurement(qk, torch, stream, n, gops)
+        precision = guarded("precision", precision_measurement, qk, torch, stream, n, gops)
     serving = None
     if args.serve_requests > 0 and world == 1:
-        serving = serving_measurement(torch, args.serve_requests)
+        serving = guarded("serving", serving_measurement, torch, args.serve_requests)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(n, circ)
+        cpu = guarded("cpu_baseline", cpu_baseline, n, circ)
 
     if rank == 0:
         line = {

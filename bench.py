@@ -91,7 +91,7 @@ DIAGONAL = {"z", "s", "sdg", "t", "tdg", "p", "rz"}
 def tile_fp32_ops(ops, n: int, tile_launches: float) -> float:
     """FP32 lane operations the fused tile passes execute for a gate list (an
     FMA counts as one): an uncontrolled non-diagonal 1-qubit gate is a pivot-form
-    butterfly, 10 operations per amplitude pair (6 FMA, 2 MUL, 2 ADD); a
+    butterfly, 8 FMAs per amplitude pair; a
     controlled one a full complex 2x2 product on the pairs where the controls
     hold, 16 per pair; diagonal gates are folded into pending phases (no
     per-gate arithmetic); each pass ends with one complex factor per amplitude
@@ -103,7 +103,7 @@ def tile_fp32_ops(ops, n: int, tile_launches: float) -> float:
         if op.kind == "swap" or op.kind in DIAGONAL:
             continue
         c = len(op.controls)
-        f += (10.0 if c == 0 else 16.0) * 2.0 ** (n - c - 1)
+        f += (8.0 if c == 0 else 16.0) * 2.0 ** (n - c - 1)
     return f + 4.0 * 2.0 ** n * tile_launches
 
 
@@ -927,7 +927,7 @@ def main():
                          "ops_per_step": ops_step,
                          "peak_kind": f"derived: {sm_count} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median SM clock "
                                       "sampled during the timed region)",
-                         "count": "10 per amplitude pair per uncontrolled non-diagonal gate, 16 per acting pair per "
+                         "count": "8 per amplitude pair per uncontrolled non-diagonal gate, 16 per acting pair per "
                                   "controlled one, 4 per amplitude per pass (final phase and scale); lower bound"}
 
     # secondary measurements: a failure in one is recorded under its key and

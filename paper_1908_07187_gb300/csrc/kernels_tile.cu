@@ -12,13 +12,13 @@
 // transposing the tile through shared memory (three fixed arrangements, see
 // qk_kernels.cuh).
 //
-// Uncontrolled gates run in pivot form (LayerGate in qk_kernels.cuh): 10 FP32
-// operations per amplitude pair (in place) instead of the 16 of a complex 2x2
-// product.  What the pivot form
-// leaves over -- a real scale, the same for every amplitude of the pass, and
-// per-qubit phases -- stays pending.  The parts that are the same for every
-// thread are tracked by the planner and folded into later gates' coefficients or
-// the final flush; each thread only keeps the parts that depend on its own bits
+// Uncontrolled gates run in pivot form (LayerGate in qk_kernels.cuh): 8 FP32
+// FMAs per amplitude pair (in place) instead of the 16 operations of a complex
+// 2x2 product.  What the pivot form leaves over -- a real scale, the same for
+// every amplitude of the pass, and per-qubit factors -- stays pending.  The parts
+// that are the same for every thread are tracked by the planner and folded into
+// later gates' coefficients or the final flush; each thread only keeps the parts
+// that depend on its own bits
 // (diagonal terms coupling a register bit with a lane, warp or fixed bit), as six
 // 32-bit fixed-point phase sums (exact modulo one turn): one per register bit
 // and one for the whole thread.  A sum of exactly half a turn is a sign flip and
@@ -33,8 +33,6 @@
 
 namespace qk {
 namespace {
-
-__host__ __device__ constexpr int ctz_const(int x) { return (x & 1) ? 0 : 1 + ctz_const(x >> 1); }
 
 constexpr uint32_t kHalfTurn = 0x80000000u;
 
@@ -202,31 +200,27 @@ __device__ __forceinline__ void flush_signs(Regs &v, uint32_t t0, const uint32_t
     }
 }
 
-// General diagonal D(r) = c0 * prod_{k in r} a_k on the 32 registers: the five
-// factors, then four independent chains over register bits 1 and 2 in Gray-code
-// order (dependency depth 4), started at c0 times the products of bits 3 and 4.
+// General diagonal D(r) = c0 * prod_{k in r} a_k on the 32 registers (any
+// magnitudes): the products of bits 3, 4 times c0 and the products of bits 1, 2
+// are formed once, then one product per float2 and one more for register bit 0.
 __device__ __forceinline__ void apply_diagonal(Regs &v, float2 c0, const float2 a[5]) {
-    float2 d[4];
+    float2 d[4], p[4];
     d[0] = c0;
     d[1] = cmul(c0, a[3]);
     d[2] = cmul(c0, a[4]);
     d[3] = cmul(d[1], a[4]);
+    p[0] = make_float2(1.f, 0.f);
+    p[1] = a[1];
+    p[2] = a[2];
+    p[3] = cmul(a[1], a[2]);
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-        const int g = l ^ (l >> 1);
-        if (l > 0) {
-            const int gp = (l - 1) ^ ((l - 1) >> 1);
-            const int bb = ctz_const(g ^ gp);      // register bit bb + 1 toggles
-            const float2 ab = a[bb + 1];
-            const float2 f = (g >> bb) & 1 ? ab : conj2(ab);
+    for (int h = 0; h < 4; ++h) {
 #pragma unroll
-            for (int h = 0; h < 4; ++h) d[h] = cmul(d[h], f);
-        }
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int j = 4 * h + g;
-            const float2 d1 = cmul(d[h], a[0]);
-            const float2 Dr = make_float2(d[h].x, d1.x), Di = make_float2(d[h].y, d1.y);
+        for (int l = 0; l < 4; ++l) {
+            const int j = 4 * h + l;   // float2 j: register bits 1, 2 = l, bits 3, 4 = h
+            const float2 D = l == 0 ? d[h] : cmul(d[h], p[l]);
+            const float2 d1 = cmul(D, a[0]);
+            const float2 Dr = make_float2(D.x, d1.x), Di = make_float2(D.y, d1.y);
             const float2 A = v.R[j], B = v.I[j];
             v.R[j] = ffma2(neg2(Di), B, __fmul2_rn(Dr, A));
             v.I[j] = ffma2(Di, A, __fmul2_rn(Dr, B));
@@ -290,46 +284,66 @@ __device__ __forceinline__ void flush_dev(Regs &v, DevPending &pd) {
 // ---------------------------------------------------------------------------
 
 // Pivot butterfly on register bit K >= 1 (see LayerGate): couples float2
-// registers (j, j | 2^(K-1)), two amplitude pairs per couple.  In place, so that
-// the results stay in the amplitudes' own registers: u = a1 y0 into temporaries,
-// then y0 += a0 y1 and y1 += u (10 packed operations per couple).
-template <int K>
-__device__ __forceinline__ void piv_packed(Regs &v, float2 a0r, float2 a0i, float2 na0i, float2 a1r, float2 a1i,
-                                           float2 na1i) {
+// registers (j, j | 2^(K-1)), two amplitude pairs per couple, in place in the
+// amplitudes' own registers.  ZF = 0: y1 += c1 y0, then y0 += c0 y1 with the new
+// y1; ZF = 1: y0 += c0 y1, then y1 += c1 y0 with the new y0.  8 packed FMAs per
+// couple.
+template <int K, int ZF>
+__device__ __forceinline__ void piv_packed(Regs &v, float2 c0r, float2 c0i, float2 nc0i, float2 c1r, float2 c1i,
+                                           float2 nc1i) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         if (j & (1 << (K - 1))) continue;
         const int j1 = j | (1 << (K - 1));
-        const float2 A = v.R[j], B = v.I[j], C = v.R[j1], D = v.I[j1];
-        const float2 ur = ffma2(na1i, B, __fmul2_rn(a1r, A));
-        const float2 ui = ffma2(a1i, A, __fmul2_rn(a1r, B));
-        v.R[j] = ffma2(na0i, D, ffma2(a0r, C, A));
-        v.I[j] = ffma2(a0i, C, ffma2(a0r, D, B));
-        v.R[j1] = __fadd2_rn(C, ur);
-        v.I[j1] = __fadd2_rn(D, ui);
+        float2 A = v.R[j], B = v.I[j], C = v.R[j1], D = v.I[j1];
+        if constexpr (ZF == 0) {
+            C = ffma2(nc1i, B, ffma2(c1r, A, C));
+            D = ffma2(c1i, A, ffma2(c1r, B, D));
+            A = ffma2(nc0i, D, ffma2(c0r, C, A));
+            B = ffma2(c0i, C, ffma2(c0r, D, B));
+        } else {
+            A = ffma2(nc0i, D, ffma2(c0r, C, A));
+            B = ffma2(c0i, C, ffma2(c0r, D, B));
+            C = ffma2(nc1i, B, ffma2(c1r, A, C));
+            D = ffma2(c1i, A, ffma2(c1r, B, D));
+        }
+        v.R[j] = A;
+        v.I[j] = B;
+        v.R[j1] = C;
+        v.I[j1] = D;
     }
 }
 
 // Pivot butterfly on register bit 0: the pair is the two halves of one float2.
-__device__ __forceinline__ void piv_bit0(Regs &v, float a0r, float a0i, float a1r, float a1i) {
+template <int ZF>
+__device__ __forceinline__ void piv_bit0(Regs &v, float c0r, float c0i, float c1r, float c1i) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        const float y0r = v.R[j].x, y0i = v.I[j].x, y1r = v.R[j].y, y1i = v.I[j].y;
-        const float ur = fmaf(-a1i, y0i, a1r * y0r), ui = fmaf(a1i, y0r, a1r * y0i);
-        v.R[j].x = fmaf(-a0i, y1i, fmaf(a0r, y1r, y0r));
-        v.I[j].x = fmaf(a0i, y1r, fmaf(a0r, y1i, y0i));
-        v.R[j].y = y1r + ur;
-        v.I[j].y = y1i + ui;
+        float y0r = v.R[j].x, y0i = v.I[j].x, y1r = v.R[j].y, y1i = v.I[j].y;
+        if constexpr (ZF == 0) {
+            y1r = fmaf(-c1i, y0i, fmaf(c1r, y0r, y1r));
+            y1i = fmaf(c1i, y0r, fmaf(c1r, y0i, y1i));
+            y0r = fmaf(-c0i, y1i, fmaf(c0r, y1r, y0r));
+            y0i = fmaf(c0i, y1r, fmaf(c0r, y1i, y0i));
+        } else {
+            y0r = fmaf(-c0i, y1i, fmaf(c0r, y1r, y0r));
+            y0i = fmaf(c0i, y1r, fmaf(c0r, y1i, y0i));
+            y1r = fmaf(-c1i, y0i, fmaf(c1r, y0r, y1r));
+            y1i = fmaf(c1i, y0r, fmaf(c1r, y0i, y1i));
+        }
+        v.R[j] = make_float2(y0r, y1r);
+        v.I[j] = make_float2(y0i, y1i);
     }
 }
 
 // One gate of a TOP_U2L layer on register bit K.  The planner folded every
-// pending phase that is the same for all threads into A0, A1 and chose the
-// stored bit order so that the pivot is the diagonal entry; the thread's own
-// pending phase e of bit K turns them into a0 = A0 e and a1 = A1 conj(e), and
-// leaves e pending on the bit.
+// pending factor that is the same for all threads into its coefficients C0, C1
+// and chose the stored bit order so that the pivot is the diagonal entry; the
+// thread's own pending phase e of bit K turns them into c0 = C0 e and
+// c1 = C1 conj(e), and leaves e pending on the bit.  zf: which value of the pair
+// is updated first (see LayerGate).
 template <int K>
-__device__ __forceinline__ void layer_gate(Regs &v, DevPending &pd, const LayerGate &g) {
+__device__ __forceinline__ void layer_gate(Regs &v, DevPending &pd, const LayerGate &g, bool zf) {
     float2 a0r = g.c[0], a0i = g.c[1], na0i = g.c[2], a1r = g.c[3], a1i = g.c[4], na1i = g.c[5];
     const uint32_t tk = pd.get(K);
     if (tk != 0u) {
@@ -344,8 +358,13 @@ __device__ __forceinline__ void layer_gate(Regs &v, DevPending &pd, const LayerG
             a1r = splat(x1.x); a1i = splat(x1.y); na1i = splat(-x1.y);
         }
     }
-    if constexpr (K == 0) piv_bit0(v, a0r.x, a0i.x, a1r.x, a1i.x);
-    else piv_packed<K>(v, a0r, a0i, na0i, a1r, a1i, na1i);
+    if constexpr (K == 0) {
+        if (zf) piv_bit0<1>(v, a0r.x, a0i.x, a1r.x, a1i.x);
+        else piv_bit0<0>(v, a0r.x, a0i.x, a1r.x, a1i.x);
+    } else {
+        if (zf) piv_packed<K, 1>(v, a0r, a0i, na0i, a1r, a1i, na1i);
+        else piv_packed<K, 0>(v, a0r, a0i, na0i, a1r, a1i, na1i);
+    }
 }
 
 // General 2x2 gate on register bit K >= 1 where the register bits in rmask are 1
@@ -581,7 +600,10 @@ __device__ __forceinline__ uint64_t tile_base(const Head &P, uint64_t tile) {
 template <typename Off>
 __device__ __forceinline__ void general_op(Regs &v, DevPending &pd, const TileOp &op, int tbits, Off base,
                                            unsigned condok) {
-    if (op.kind == TOP_U2) pd.add(op.k, op.hturns);  // uniform part, in every thread
+    if (op.kind == TOP_U2) {   // uniform part of the target's pending factor, in every thread
+        pd.add(op.k, op.hturns);
+        if (op.hmag != 1.f) bit_factor_dispatch(op.k, v, make_float2(op.hmag, 0.f));
+    }
     if (!op_applies<Off>(op, tbits, base, condok)) return;
     if (op.kind == TOP_PAIR) {
         pair_dispatch(v, op.k, make_float2(op.ph.re, op.ph.im), op.rval);
@@ -673,6 +695,7 @@ struct OpHead {
     uint32_t w0, w1, w2, w3;
     __device__ __forceinline__ int kind() const { return (int)(w0 & 0xffu); }
     __device__ __forceinline__ int k() const { return (int)((w0 >> 8) & 0xffu); }
+    __device__ __forceinline__ int rmask() const { return (int)((w0 >> 16) & 0xffu); }   // TOP_U2L: zf mask
     __device__ __forceinline__ int rval() const { return (int)(w0 >> 24); }
     __device__ __forceinline__ int count() const { return (int)(w2 >> 16); }
     __device__ __forceinline__ int first() const { return (int)(w3 & 0xffffu); }
@@ -744,12 +767,12 @@ __device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ p
             switch (h.kind()) {
                 case TOP_U2L: {
                     const LayerGate *lg = &pr.lg(h.first());
-                    const int bits = h.k();
-                    if (bits & 1) layer_gate<0>(v, pd, *lg++);
-                    if (bits & 2) layer_gate<1>(v, pd, *lg++);
-                    if (bits & 4) layer_gate<2>(v, pd, *lg++);
-                    if (bits & 8) layer_gate<3>(v, pd, *lg++);
-                    if (bits & 16) layer_gate<4>(v, pd, *lg);
+                    const int bits = h.k(), zf = h.rmask();
+                    if (bits & 1) layer_gate<0>(v, pd, *lg++, zf & 1);
+                    if (bits & 2) layer_gate<1>(v, pd, *lg++, zf & 2);
+                    if (bits & 4) layer_gate<2>(v, pd, *lg++, zf & 4);
+                    if (bits & 8) layer_gate<3>(v, pd, *lg++, zf & 8);
+                    if (bits & 16) layer_gate<4>(v, pd, *lg, zf & 16);
                     if (h.czmask()) cz_mask(v, h.czmask());
                     break;
                 }
@@ -814,33 +837,45 @@ __device__ __forceinline__ void tile_body(const Prog &pr, float2 *__restrict__ p
         }
 
         // final flush: the thread's own pending phases plus the planner's uniform
-        // ones (register bits, and lane / warp bits as a thread constant) and the
-        // pass's real scale.  The store arrangement is ARR_IO or ARR_HI: lanes =
+        // factors (register bits, and lane / warp bits as a thread constant; each a
+        // phase and a magnitude) and the pass's real scale.  The store arrangement is ARR_IO or ARR_HI: lanes =
         // local 0..4 in both; registers local 5..9 / 8..12, warps local 10..12 / 5..7.
         {
             const int rb = cur == ARR_IO ? 5 : 8, wb = cur == ARR_IO ? 10 : 5;
             uint32_t t0 = pd.get0() + P.fin_turns[13];
+            float mg = P.fin_scale;   // the thread's constant magnitude
             for (uint64_t fm = P.fin_fixed_mask; fm; fm &= fm - 1) {
                 const int b = __ffsll((long long)fm) - 1;
-                if ((tile >> b) & 1) t0 += P.fin_fixed[b];
+                if ((tile >> b) & 1) {
+                    t0 += P.fin_fixed[b];
+                    mg *= P.fin_fixed_mag[b];
+                }
             }
 #pragma unroll
             for (int j = 0; j < 5; ++j)
-                if ((lane >> j) & 1) t0 += P.fin_turns[j];
+                if ((lane >> j) & 1) {
+                    t0 += P.fin_turns[j];
+                    mg *= P.fin_mag[j];
+                }
 #pragma unroll
             for (int j = 0; j < 3; ++j)
-                if ((warp >> j) & 1) t0 += P.fin_turns[wb + j];
+                if ((warp >> j) & 1) {
+                    t0 += P.fin_turns[wb + j];
+                    mg *= P.fin_mag[wb + j];
+                }
             float2 a[5];
-            bool any = t0 != 0u || P.fin_scale != 1.f;
+            bool any = t0 != 0u || mg != 1.f;
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 const uint32_t tk = pd.get(k) + P.fin_turns[rb + k];
-                any = any || tk != 0u;
-                a[k] = phase_of(tk);
+                const float mk = P.fin_mag[rb + k];
+                any = any || tk != 0u || mk != 1.f;
+                const float2 e = phase_of(tk);
+                a[k] = make_float2(e.x * mk, e.y * mk);
             }
             if (any) {
                 const float2 c0 = phase_of(t0);
-                apply_diagonal(v, make_float2(c0.x * P.fin_scale, c0.y * P.fin_scale), a);
+                apply_diagonal(v, make_float2(c0.x * mg, c0.y * mg), a);
             }
         }
 

@@ -281,9 +281,11 @@ constexpr int kTileMaxMats = 160;
 constexpr int kTileMaxConds = 4;
 enum TileArr : uint8_t { ARR_IO = 0, ARR_LO = 1, ARR_HI = 2 };
 // TOP_U2L: a layer of uncontrolled 2x2 gates on distinct register bits (k is
-// the bit mask), in pivot form; their coefficients are lg[first...] in bit order.
-// After the gates, a CZ between register bits (k, l) for every bit set in tmask
-// (bit cz_index(k, l) over the ten pairs, see below).
+// the bit mask), in pivot form; their coefficients are lg[first...] in bit order,
+// and bit b of rmask says that the gate on register bit b updates the pair's
+// stored |0> value first (LayerGate).  After the gates, a CZ between register
+// bits (k, l) for every bit set in tmask (bit cz_index(k, l) over the ten pairs,
+// see below).
 // TOP_PHASEL: a group of thread- or tile-dependent diagonal terms that all add to
 // one pending phase sum (register bit k, or the thread constant when k == 5):
 // lin[first, first + count), evaluated in place (see LinTerm); rval = 1 says that
@@ -330,16 +332,21 @@ struct LinTerm {
 // qubit's two values stored swapped ("flipped"); it picks the stored order of the
 // gate's output so that, with M the gate in stored order and the pending factor F
 // of the bit folded in, M diag(1, F) has its larger entries on the diagonal
-// (|M00| = |M11| >= |M10| = |M01|).  It is applied to a pair (y0, y1) as
-//   z0 = y0 + a0 y1,  z1 = y1 + a1 y0,   a0 = M01 F / M00,  a1 = M10 / (M11 F),
-// and the true outputs are (M00 z0, M11 F z1): |a0|, |a1| <= 1, and 10 FP32
-// operations per pair in place (u = a1 y0; y0 += a0 y1; y1 += u).
-// |M00| >= 1/sqrt 2 is one real scale for the whole pass and the phases of M00
-// and M11 F / M00 become pending phases, both tracked by the planner.  The
-// device uses a0 = A0 e and a1 = A1 conj(e), with e the thread-dependent part of
-// F; c[] holds A0, A1 as FFMA2 operand pairs (re, re), (im, im), (-im, -im).
+// (|M00| = |M11| >= |M10| = |M01|).  With a0 = M01 F / M00, a1 = M10 / (M11 F)
+// the true outputs are (M00 z0, M11 F z1) for z0 = y0 + a0 y1, z1 = y1 + a1 y0.
+// The device forms them in place from one value of the pair to the other, 8
+// FP32 FMAs per pair:
+//   zf = 0:  y1 += a1 y0,  then y0 += s a0 y1   (y0 ends as s z0, y1 as z1)
+//   zf = 1:  y0 += a0 y1,  then y1 += s a1 y0   (y0 ends as z0, y1 as s z1)
+// with s = 1 / (1 - a0 a1).  For a unitary M, a0 a1 = -|M01|^2 / |M00|^2, so s
+// = |M00|^2 is real and in [1/2, 1]; the planner keeps the leftover factor (M00 /
+// s and M11 F, or M00 and M11 F / s) as pending: a real scale and a phase for the
+// whole pass, and a factor of magnitude in [1/2, 2] on the bit's |1> (it picks zf
+// per gate so that the magnitude stays there).  The device uses c0 = C0 e and
+// c1 = C1 conj(e), with e the thread-dependent part of F; c[] holds C0 (s a0 or
+// a0) and C1 (a1 or s a1) as FFMA2 operand pairs (re, re), (im, im), (-im, -im).
 struct LayerGate {
-    float2 c[6];           // A0r, A0i, -A0i, A1r, A1i, -A1i, each splatted
+    float2 c[6];           // C0r, C0i, -C0i, C1r, C1i, -C1i, each splatted
 };
 
 struct TileOp {
@@ -353,7 +360,8 @@ struct TileOp {
     uint16_t count2;
     uint32_t hturns;       // TOP_U2: uniform pending turns of the target's qubit, added
                            // to the thread's pending sum before the op
-    uint32_t pad;
+    float hmag;            // TOP_U2: uniform pending magnitude of the target's |1>,
+                           // applied to the amplitudes before the op (1: none)
     uint64_t gmask, gval;  // condition on the tile's fixed (non-tile) physical bits
     union {
         float m[8];        // U2: m00, m01, m10, m11 as (re, im)
@@ -387,16 +395,18 @@ struct TileHead {
     int n_conds;
     Cond conds[kTileMaxConds];
     int nops;
-    // final flush: the uniform pending phase of each local qubit's |1> (turns), the
-    // uniform constant phase (fin_turns[13]) and the real scale; a plan's last pass
-    // also applies the phases that earlier passes left on qubits outside its S:
-    // fin_fixed[b] turns where tile-index bit b (qubit fixed[b]) is 1, for the bits
-    // set in fin_fixed_mask
+    // final flush: the uniform pending factor of each local qubit's |1> (phase in
+    // turns and magnitude), the uniform constant phase (fin_turns[13]) and the real
+    // scale; a plan's last pass also applies the factors that earlier passes left on
+    // qubits outside its S: fin_fixed[b] turns and fin_fixed_mag[b] where tile-index
+    // bit b (qubit fixed[b]) is 1, for the bits set in fin_fixed_mask
     uint32_t fin_turns[14];
+    float fin_mag[kTileQubits];
     float fin_scale;
     int need_tab;          // 0: every phase the pass can form is 0 or half a turn
     uint64_t fin_fixed_mask;
     uint32_t fin_fixed[40];
+    float fin_fixed_mag[40];
     int fin_flip;          // local qubits stored flipped at the end (bit b: local qubit b)
     int nlg, nlin;         // entries of lg[] and lin[] in use
 };

@@ -14,9 +14,10 @@
 //
 // A last walk over the program (fold_program) turns each layer gate into pivot
 // form (LayerGate in qk_kernels.cuh) and keeps, in double precision, every
-// pending phase that is the same for all threads -- per local qubit, plus a
-// constant -- and the pass's real scale: those fold into later gates'
-// coefficients and the final flush, so the device never sees them.
+// pending factor that is the same for all threads -- per local qubit (a phase and
+// a magnitude), plus a constant phase -- and the pass's real scale: those fold
+// into later gates' coefficients and the final flush, so the device never sees
+// them.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -149,21 +150,28 @@ struct Mat2 {
 };
 
 // The program's pending state that is the same for every thread, in double
-// precision: u[q] the phase of local qubit q's stored |1> relative to its stored
-// |0>, u0 a constant phase, lam the real scale that the pivot form leaves over,
-// flip[q] whether q's values are stored swapped.
+// precision: mag[q] e^{i u[q]} the factor of local qubit q's stored |1> relative
+// to its stored |0>, u0 a constant phase, lam the real scale that the pivot form
+// leaves over, flip[q] whether q's values are stored swapped.
 struct UniformPending {
-    double u[kTileQubits] = {};
+    double u[kTileQubits] = {};     // phase of the pending factor on a local qubit's stored |1>
+    double mag[kTileQubits];        // its magnitude (in [1/2, 2])
     double u0 = 0.0;
     double lam = 1.0;
     int flip[kTileQubits] = {};   // local qubit stored with its two values swapped
+    UniformPending() {
+        for (double &m : mag) m = 1.0;
+    }
 };
 
 // Pivot form of a layer gate on local qubit q (LayerGate in qk_kernels.cuh).  The
 // gate in stored order is W = U X^f (f: q stored flipped); the output is stored
 // flipped (f') when that puts the larger entries of M = X^f' W on the diagonal.
-// F = e^{i u[q]} is the pending phase of q's stored |1>.
-void pivot_gate(const Mat2 &g, UniformPending &st, int q, LayerGate &out) {
+// F = mag[q] e^{i u[q]} is the pending factor of q's stored |1>.  Returns zf, the
+// value of the pair the device updates first: the one that keeps the pending
+// magnitude of q's |1> within [1/2, 2] (zf = 0 multiplies it by s <= 1, zf = 1
+// divides it by s >= 1/2).
+int pivot_gate(const Mat2 &g, UniformPending &st, int q, LayerGate &out) {
     cdm W[4] = {g.m[0], g.m[1], g.m[2], g.m[3]};
     if (st.flip[q]) {  // U X: swap the columns
         std::swap(W[0], W[1]);
@@ -175,19 +183,28 @@ void pivot_gate(const Mat2 &g, UniformPending &st, int q, LayerGate &out) {
         std::swap(W[1], W[3]);
     }
     const cdm m00 = W[0], m01 = W[1], m10 = W[2], m11 = W[3];
-    const cdm F = std::polar(1.0, st.u[q]);
+    const cdm F = std::polar(st.mag[q], st.u[q]);
     const cdm A0 = m01 * F / m00, A1 = m10 / (m11 * F);
-    st.u0 += std::arg(m00);
-    st.u[q] += std::arg(m11) - std::arg(m00);
-    st.lam *= std::abs(m00);
+    // y1 += a1 y0 then y0 += s a0 y1 leaves y0 = s z0 (and the other order y1 =
+    // s z1) for s = 1 / (1 - a0 a1), real and in [1/2, 1] for a unitary gate
+    const cdm s = 1.0 / (1.0 - A0 * A1);
+    const int zf = st.mag[q] < 1.0 ? 1 : 0;
+    const cdm C0 = zf ? A0 : s * A0, C1 = zf ? s * A1 : A1;
+    const cdm P0 = zf ? m00 : m00 / s, P1 = zf ? m11 * F / s : m11 * F;   // the true outputs' factors
+    st.u0 += std::arg(P0);
+    st.lam *= std::abs(P0);
+    const cdm R = P1 / P0;
+    st.u[q] = std::arg(R);
+    st.mag[q] = std::abs(R);
     st.flip[q] = fout ? 1 : 0;
-    const float a0r = (float)A0.real(), a0i = (float)A0.imag(), a1r = (float)A1.real(), a1i = (float)A1.imag();
+    const float a0r = (float)C0.real(), a0i = (float)C0.imag(), a1r = (float)C1.real(), a1i = (float)C1.imag();
     out.c[0] = make_float2(a0r, a0r);
     out.c[1] = make_float2(a0i, a0i);
     out.c[2] = make_float2(-a0i, -a0i);
     out.c[3] = make_float2(a1r, a1r);
     out.c[4] = make_float2(a1i, a1i);
     out.c[5] = make_float2(-a1i, -a1i);
+    return zf;
 }
 
 // local qubits of the thread bits (0..4 lanes, 5..7 warps) in an arrangement
@@ -212,6 +229,8 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
     // qubit, on its |1>, plus a constant phase and a real scale; only the plan's
     // last pass applies them to the amplitudes
     double carry[64] = {0.0};
+    double carry_mag[64];
+    for (double &m : carry_mag) m = 1.0;
     double carry_u0 = 0.0, carry_lam = 1.0;
     // The gates one pass takes from rem for a qubit set S: in order, each gate
     // that commutes with every gate left behind before it, whose 2x2 target is in
@@ -658,7 +677,10 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
             // device, and what is left goes to the final flush
             {
                 UniformPending st;
-                for (int q = 0; q < kTileQubits; ++q) st.u[q] = carry[(int)P.S[q]];
+                for (int q = 0; q < kTileQubits; ++q) {
+                    st.u[q] = carry[(int)P.S[q]];
+                    st.mag[q] = carry_mag[(int)P.S[q]];
+                }
                 st.u0 = carry_u0;
                 st.lam = carry_lam;
                 int arr = ARR_IO, w = 0;
@@ -692,7 +714,7 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
                                 if (!((o.k >> b) & 1)) continue;
                                 const FusedOp &fo = *taken[lg_mat[idx]].op;
                                 const Mat2 g{{fo.m[0], fo.m[1], fo.m[2], fo.m[3]}};
-                                pivot_gate(g, st, qk_of(b), P.lg[idx]);
+                                if (pivot_gate(g, st, qk_of(b), P.lg[idx])) o.rmask |= (uint8_t)(1u << b);
                                 ++idx;
                             }
                             break;
@@ -794,7 +816,9 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
                                 }
                             }
                             o.hturns = angle_turns(st.u[q]);
+                            o.hmag = (float)st.mag[q];
                             st.u[q] = 0.0;
+                            st.mag[q] = 1.0;
                             break;
                         }
                         default:
@@ -819,31 +843,40 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
                 for (int q = 0; q < kTileQubits; ++q) P.fin_flip |= st.flip[q] << q;
                 P.fin_fixed_mask = 0;
                 if (left.empty()) {   // the plan's last pass applies everything pending
-                    for (int q = 0; q < kTileQubits; ++q) P.fin_turns[q] = angle_turns(st.u[q]);
+                    for (int q = 0; q < kTileQubits; ++q) {
+                        P.fin_turns[q] = angle_turns(st.u[q]);
+                        P.fin_mag[q] = (float)st.mag[q];
+                    }
                     P.fin_turns[13] = angle_turns(st.u0);
                     P.fin_scale = (float)st.lam;
                     for (int b = 0; b < P.nfix; ++b) {
                         const uint32_t t = angle_turns(carry[(int)P.fixed[b]]);
                         P.fin_fixed[b] = t;
-                        if (t) P.fin_fixed_mask |= 1ull << b;
+                        P.fin_fixed_mag[b] = (float)carry_mag[(int)P.fixed[b]];
+                        if (t || P.fin_fixed_mag[b] != 1.f) P.fin_fixed_mask |= 1ull << b;
                     }
                 } else {              // hand the uniform part to the next pass
                     for (int q = 0; q < kTileQubits; ++q) {
-                        // a qubit stored flipped has its phase on |0>: e^{iu} on |0> is
-                        // e^{iu} overall times e^{-iu} on |1>
+                        // a qubit stored flipped has its factor F on |0>: F on |0> is F
+                        // overall times 1 / F on |1>
                         const int pq = (int)P.S[q];
                         if (st.flip[q]) {
                             carry[pq] = -st.u[q];
+                            carry_mag[pq] = 1.0 / st.mag[q];
                             st.u0 += st.u[q];
+                            st.lam *= st.mag[q];
                         } else {
                             carry[pq] = st.u[q];
+                            carry_mag[pq] = st.mag[q];
                         }
                         P.fin_turns[q] = 0;
+                        P.fin_mag[q] = 1.f;
                     }
                     carry_u0 = st.u0;
                     P.fin_turns[13] = 0;
                     // the stored amplitudes are the true ones divided by the scale
-                    // (>= 2^-1/2 per gate): keep them within 2^24 of it in FP32
+                    // (a factor in [2^-1/2, 2] per gate): keep them within 2^24 of it
+                    // in FP32
                     if (st.lam < 0x1p-24 || st.lam > 0x1p24) {
                         P.fin_scale = (float)st.lam;
                         carry_lam = 1.0;

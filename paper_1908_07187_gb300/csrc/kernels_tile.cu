@@ -201,24 +201,17 @@ __device__ __forceinline__ void flush_signs(Regs &v, uint32_t t0, const uint32_t
 }
 
 // General diagonal D(r) = c0 * prod_{k in r} a_k on the 32 registers (any
-// magnitudes): the products of bits 3, 4 times c0 and the products of bits 1, 2
-// are formed once, then one product per float2 and one more for register bit 0.
+// magnitudes): per value of register bits 1, 2 the factor q = c0 a1^r1 a2^r2,
+// then per value of bits 3, 4 one more product, and one for register bit 0.
 __device__ __forceinline__ void apply_diagonal(Regs &v, float2 c0, const float2 a[5]) {
-    float2 d[4], p[4];
-    d[0] = c0;
-    d[1] = cmul(c0, a[3]);
-    d[2] = cmul(c0, a[4]);
-    d[3] = cmul(d[1], a[4]);
-    p[0] = make_float2(1.f, 0.f);
-    p[1] = a[1];
-    p[2] = a[2];
-    p[3] = cmul(a[1], a[2]);
+    const float2 a12 = cmul(a[1], a[2]), a34 = cmul(a[3], a[4]);
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
+    for (int l = 0; l < 4; ++l) {
+        const float2 q = l == 0 ? c0 : cmul(c0, l == 1 ? a[1] : l == 2 ? a[2] : a12);
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {
+        for (int h = 0; h < 4; ++h) {
             const int j = 4 * h + l;   // float2 j: register bits 1, 2 = l, bits 3, 4 = h
-            const float2 D = l == 0 ? d[h] : cmul(d[h], p[l]);
+            const float2 D = h == 0 ? q : cmul(q, h == 1 ? a[3] : h == 2 ? a[4] : a34);
             const float2 d1 = cmul(D, a[0]);
             const float2 Dr = make_float2(D.x, d1.x), Di = make_float2(D.y, d1.y);
             const float2 A = v.R[j], B = v.I[j];

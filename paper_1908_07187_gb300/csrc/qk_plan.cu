@@ -236,7 +236,10 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
     // that commutes with every gate left behind before it, whose 2x2 target is in
     // S (with grow, a target joins S while S has room) and whose classical
     // condition fits the condition table.  Counts only when tk is null.
+    // Once every qubit carries a left-behind 2x2 gate, no later gate commutes with
+    // them all, so the walk stops there (the rest is left behind as a whole).
     std::vector<Cond> conds;
+    const uint64_t all_qubits = n >= 64 ? ~0ull : (1ull << n) - 1;
     auto take = [&](uint64_t S0, bool grow, std::vector<POp> *tk, std::vector<POp> *lf, uint64_t *S_out,
                     int *n_u2_out, int *n_ph_out) {
         uint64_t S = S0;
@@ -244,7 +247,12 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
         uint64_t ndb = 0, allb = 0;
         int n_u2 = 0, n_ph = 0;
         conds.clear();
-        for (const POp &p : rem) {
+        for (auto it = rem.begin(); it != rem.end(); ++it) {
+            if (ndb == all_qubits) {
+                if (lf) lf->insert(lf->end(), it, rem.end());
+                break;
+            }
+            const POp &p = *it;
             const bool is_u2 = p.op->kind == FusedOp::U2;
             bool ok = (is_u2 ? n_u2 < max_u2 : n_ph < max_ph) && !(p.nd & allb) && !(p.all & ndb);
             if (ok && is_u2) {

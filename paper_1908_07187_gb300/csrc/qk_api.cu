@@ -8,7 +8,9 @@
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
@@ -20,6 +22,59 @@
 #include "qk_plan.h"
 
 using cd = std::complex<double>;
+
+namespace qk {
+namespace {
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kPoolDevices] = {};
+int g_pool_users[kPoolDevices] = {};
+}  // namespace
+
+cudaMemPool_t pool_acquire(int device) {
+    if (device < 0 || device >= kPoolDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[device]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;   // keep freed blocks for reuse
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cudaGetLastError();
+            cudaMemPoolDestroy(pool);
+            return nullptr;
+        }
+        g_pool[device] = pool;
+    }
+    ++g_pool_users[device];
+    return g_pool[device];
+}
+
+void pool_release(int device) {
+    if (device < 0 || device >= kPoolDevices) return;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[device] || g_pool_users[device] <= 0) return;
+    if (--g_pool_users[device] == 0) cudaMemPoolTrimTo(g_pool[device], 0);   // the last holder: give it all back
+}
+
+cudaError_t pool_malloc(void **p, size_t bytes, int device, cudaStream_t s) {
+    cudaMemPool_t pool = nullptr;
+    if (device >= 0 && device < kPoolDevices) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        pool = g_pool[device];
+    }
+    if (pool) return cudaMallocFromPoolAsync(p, bytes, pool, s);
+    return cudaMallocAsync(p, bytes, s);
+}
+}  // namespace qk
 
 namespace {
 
@@ -50,6 +105,7 @@ struct qk_ctx {
     size_t amp = 8;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    bool pool_held = false;   // holds the library's memory pool of its device
     int device = 0;
     int sms = 148;
     qk_options opt{};
@@ -117,10 +173,12 @@ qk_status fail(qk_ctx *c, qk_status s, const char *fmt, ...) {
 
 size_t full_pass_bytes(const qk_ctx *c) { return (size_t)2 * c->amp << c->n; }
 
-// Device memory is stream-ordered on the context's stream (cudaMallocAsync /
-// cudaFreeAsync): freeing a finished context does not synchronise the device, so
-// other contexts' work keeps running (the serving loop relies on this).
-cudaError_t dalloc(qk_ctx *c, void **p, size_t bytes) { return cudaMallocAsync(p, bytes, c->stream); }
+
+// Device memory is stream-ordered on the context's stream (from the library's
+// pool, freed with cudaFreeAsync): freeing a finished context does not
+// synchronise the device, so other contexts' work keeps running (the serving
+// loop relies on this).
+cudaError_t dalloc(qk_ctx *c, void **p, size_t bytes) { return qk::pool_malloc(p, bytes, c->device, c->stream); }
 void dfree(qk_ctx *c, void *p) {
     if (p) cudaFreeAsync(p, c->stream);
 }
@@ -527,6 +585,7 @@ qk_status qk_create(qk_ctx **out, qk_precision precision, void *cuda_stream, con
         if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return QK_ECUDA; }
         c->own_stream = true;
     }
+    c->pool_held = qk::pool_acquire(c->device) != nullptr;
     c->meas_blocks = c->sms * kMeasBlocksPerSM;
     if (dalloc(c, (void **)&c->d_partials, sizeof(double) * 2 * c->meas_blocks) != cudaSuccess ||
         dalloc(c, (void **)&c->d_err, sizeof(int)) != cudaSuccess ||
@@ -563,6 +622,7 @@ qk_status qk_destroy(qk_ctx *c) {
     dfree(c, c->d_partials);
     dfree(c, c->d_slots);
     if (c->stream) cudaStreamSynchronize(c->stream);   // this stream only
+    if (c->pool_held) qk::pool_release(c->device);     // after its blocks went back to the pool
     if (c->planner) qk::free_planner(c->planner);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -301,6 +301,8 @@ __global__ void k_set_basis0(float2 *pool, const uint64_t *offs, int count) {
 struct qk_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    int device = 0;
+    bool pool_held = false;   // holds the library's memory pool of its device
     int sms = 148;
     std::vector<qk::BOp> ops;
     std::vector<qk::BCirc> circs;
@@ -373,14 +375,16 @@ bool cur_circuit(qk_batch *b, qk::BCirc **c) {
     return true;
 }
 
+// Device buffers are stream-ordered on the batch's stream (the library's pool):
+// growing one does not synchronise the device while other streams run.
 template <typename T>
 qk_status grow(qk_batch *b, T **p, size_t *cap, size_t need) {
     if (need <= *cap) return QK_OK;
     size_t nc = std::max(need, *cap * 2);
-    if (*p) cudaFree(*p);
+    if (*p) cudaFreeAsync(*p, b->stream);
     *p = nullptr;
     *cap = 0;
-    if (cudaMalloc((void **)p, sizeof(T) * nc) != cudaSuccess) {
+    if (qk::pool_malloc((void **)p, sizeof(T) * nc, b->device, b->stream) != cudaSuccess) {
         cudaGetLastError();
         return bfail(b, QK_ENOMEM, "batch: cannot allocate %zu bytes", sizeof(T) * nc);
     }
@@ -585,6 +589,14 @@ qk_status run_large(qk_batch *b) {
 
 }  // namespace
 
+namespace {
+// device -> host copy on the batch's stream, complete on return
+bool read_back(qk_batch *b, void *dst, const void *src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, b->stream) == cudaSuccess &&
+           cudaStreamSynchronize(b->stream) == cudaSuccess;
+}
+}  // namespace
+
 extern "C" {
 
 qk_status qk_batch_create(qk_batch **out, void *cuda_stream) {
@@ -599,6 +611,8 @@ qk_status qk_batch_create(qk_batch **out, void *cuda_stream) {
         delete b;
         return QK_ECUDA;
     }
+    b->device = dev;
+    b->pool_held = qk::pool_acquire(dev) != nullptr;
     if (cuda_stream) {
         b->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -618,18 +632,14 @@ qk_status qk_batch_create(qk_batch **out, void *cuda_stream) {
 
 qk_status qk_batch_destroy(qk_batch *b) {
     if (!b) return QK_EINVAL;
-    if (b->stream) cudaStreamSynchronize(b->stream);
-    cudaFree(b->d_ops);
-    cudaFree(b->d_circs);
-    cudaFree(b->d_states);
-    cudaFree(b->d_cbits);
-    cudaFree(b->d_lstates);
-    cudaFree(b->d_lprogs);
-    cudaFree(b->d_lfirst);
-    cudaFree(b->d_loffs);
-    cudaFree(b->d_lops);
-    cudaFree(b->d_llg);
-    cudaFree(b->d_llin);
+    if (b->stream) {
+        void *bufs[] = {b->d_ops, b->d_circs, b->d_states, b->d_cbits, b->d_lstates, b->d_lprogs,
+                        b->d_lfirst, b->d_loffs, b->d_lops, b->d_llg, b->d_llin};
+        for (void *q : bufs)
+            if (q) cudaFreeAsync(q, b->stream);
+        cudaStreamSynchronize(b->stream);
+    }
+    if (b->pool_held) qk::pool_release(b->device);   // after its blocks went back to the pool
     if (b->h_stage) cudaFreeHost(b->h_stage);
     if (b->done) cudaEventDestroy(b->done);
     if (b->start) cudaEventDestroy(b->start);
@@ -924,11 +934,11 @@ qk_status qk_batch_read(qk_batch *b, int circuit, uint8_t *cbits, int ncb, void 
     if (state && ((!large && !b->store_state) || bytes != sizeof(float2) << c.n))
         return bfail(b, QK_EINVAL, "batch: state not stored or wrong size (%zu bytes expected)", sizeof(float2) << c.n);
     if (cudaEventSynchronize(b->done) != cudaSuccess) return bfail(b, QK_ECUDA, "batch: event wait failed");
-    if (ncb > 0 && cudaMemcpy(cbits, b->d_cbits + c.cb_off, ncb, cudaMemcpyDeviceToHost) != cudaSuccess)
+    // reads on the batch's own stream (its run is complete: the event above)
+    if (ncb > 0 && !read_back(b, cbits, b->d_cbits + c.cb_off, ncb))
         return bfail(b, QK_ECUDA, "batch: cbit copy failed");
     const float2 *src = large ? b->d_lstates + b->large[b->large_of[circuit]].state_off : b->d_states + c.state_off;
-    if (state && cudaMemcpy(state, src, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return bfail(b, QK_ECUDA, "batch: state copy failed");
+    if (state && !read_back(b, state, src, bytes)) return bfail(b, QK_ECUDA, "batch: state copy failed");
     return QK_OK;
 }
 
@@ -936,8 +946,7 @@ qk_status qk_batch_read_all_cbits(qk_batch *b, uint8_t *out, size_t n) {
     if (!b) return QK_EINVAL;
     if (n != b->total_cb || (n > 0 && !out)) return bfail(b, QK_EINVAL, "batch: need %u cbit bytes", b->total_cb);
     if (cudaEventSynchronize(b->done) != cudaSuccess) return bfail(b, QK_ECUDA, "batch: event wait failed");
-    if (n > 0 && cudaMemcpy(out, b->d_cbits, n, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return bfail(b, QK_ECUDA, "batch: cbit copy failed");
+    if (n > 0 && !read_back(b, out, b->d_cbits, n)) return bfail(b, QK_ECUDA, "batch: cbit copy failed");
     return QK_OK;
 }
 

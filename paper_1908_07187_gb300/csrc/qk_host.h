@@ -5,6 +5,8 @@
 #include <complex>
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
 #include "qk.h"
 
 namespace qk {
@@ -62,6 +64,21 @@ inline bool builtin_matrix(int id, const double *p, int np, cd m[4], int &ntarge
         default: return false;
     }
 }
+
+// The library's stream-ordered device memory (contexts and batches) comes from
+// one memory pool per device that keeps freed blocks for reuse.  A pool whose
+// release threshold is 0 (the default pool's) hands freed memory back to the
+// system at every stream or event synchronisation; with multi-GiB states that
+// unmapping took up to ~0.2 s per synchronisation and stalled callers that free
+// one state while others run.  Every context and batch holds the pool of its
+// device from creation to destruction; when the last one on a device goes, the
+// pool is trimmed back to empty.
+// pool_acquire returns the pool (nullptr if it cannot be created: callers then
+// use the device's default pool); pool_release drops one holder.
+cudaMemPool_t pool_acquire(int device);
+void pool_release(int device);
+// stream-ordered allocation from the device's pool (or the default pool)
+cudaError_t pool_malloc(void **p, size_t bytes, int device, cudaStream_t s);
 
 // Inverse of a mod N by the extended Euclidean algorithm; ok = (gcd(a, N) == 1).
 inline uint64_t modinv(uint64_t a, uint64_t N, bool &ok) {

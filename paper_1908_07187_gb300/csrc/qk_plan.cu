@@ -225,9 +225,9 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
     // kernel-parameter budget (ops and grouped phase entries)
     int max_u2 = 100, max_ph = 300;
     std::vector<POp> left, taken;
-    // the uniform pending phases one pass leaves to the next (FP64): per physical
-    // qubit, on its |1>, plus a constant phase and a real scale; only the plan's
-    // last pass applies them to the amplitudes
+    // the uniform pending factors one pass leaves to the next (FP64): per physical
+    // qubit, on its |1> (a phase and a magnitude), plus a constant phase and a real
+    // scale; only the plan's last pass applies them to the amplitudes
     double carry[64] = {0.0};
     double carry_mag[64];
     for (double &m : carry_mag) m = 1.0;

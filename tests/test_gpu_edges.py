@@ -109,3 +109,22 @@ def test_bounded_wait_timeout_is_reported_and_context_stays_usable(qk):
     ref.apply_matrix(oracle.GATES_1Q["h"], [2])
     np.testing.assert_allclose(ctx.get_state(), ref.psi, atol=1e-5)
     ctx.close()
+
+
+def test_freed_state_memory_is_reused(qk):
+    """The library keeps freed device memory in its own pool for reuse (and trims
+    it when its last context or batch goes): creating and destroying a 2 GiB state
+    three times holds at most one such block, never three."""
+    import torch
+
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        ctx = qk.Context("c64", "fused")
+        ctx.add_qubits(28)
+        ctx.apply_gate("h", [27])
+        ctx.sync()
+        ctx.close()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free0 - free1 < int(2.5 * 2**30), (free0, free1)

@@ -360,14 +360,28 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
 
         // ---- list-schedule the taken gates over the arrangements
         const int m = (int)taken.size();
-        std::vector<int> npred(m, 0);
-        std::vector<std::vector<int>> succ(m);
+        // dependency edges i -> j (i < j, not commuting) as flat successor lists:
+        // the successors of i are succ[succ_at[i] .. succ_at[i + 1])
+        static thread_local std::vector<int> npred, succ_at, succ, edge_i, edge_j;
+        npred.assign(m, 0);
+        succ_at.assign(m + 1, 0);
+        edge_i.clear();
+        edge_j.clear();
         for (int j = 0; j < m; ++j)
             for (int i = 0; i < j; ++i)
                 if (!commute(taken[i], taken[j])) {
                     npred[j]++;
-                    succ[i].push_back(j);
+                    succ_at[i + 1]++;
+                    edge_i.push_back(i);
+                    edge_j.push_back(j);
                 }
+        for (int i = 0; i < m; ++i) succ_at[i + 1] += succ_at[i];
+        succ.resize(edge_i.size());
+        {
+            static thread_local std::vector<int> fill;
+            fill.assign(succ_at.begin(), succ_at.end() - 1);
+            for (size_t e = 0; e < edge_i.size(); ++e) succ[fill[edge_i[e]]++] = edge_j[e];   // ascending j per i
+        }
         std::vector<char> done(m, 0);
         int ndone = 0, cur = ARR_IO, nops = 0;
         static thread_local std::vector<TileOp> prog;
@@ -403,7 +417,7 @@ qk_status plan_passes(TilePlanner *planner, int n, const std::vector<FusedOp> &o
             }
             done[j] = 1;
             ++ndone;
-            for (int s : succ[j]) npred[s]--;
+            for (int e = succ_at[j]; e < succ_at[j + 1]; ++e) npred[succ[e]]--;
         };
         while (ndone < m) {
             bool progress = false;

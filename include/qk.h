@@ -21,7 +21,10 @@
  *
  * Ownership: every input array is copied (or consumed) before the call returns;
  * the context owns all device memory it allocates; outputs go into caller
- * buffers.  Errors: every call returns a qk_status; nothing throws across the ABI.
+ * buffers.  Device memory is taken stream-ordered from one memory pool per device
+ * that the library keeps: blocks freed by a destroyed context or batch stay in it
+ * for reuse while any context or batch exists on that device, and the pool is
+ * trimmed to empty when the last one is destroyed.  Errors: every call returns a qk_status; nothing throws across the ABI.
  * A call that fails argument checks leaves the context unchanged and sets the
  * message returned by qk_last_error.  A QK_ECUDA status means a CUDA call failed;
  * the context should then be destroyed.

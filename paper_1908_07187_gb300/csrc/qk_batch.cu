@@ -45,7 +45,9 @@ constexpr int kBMaxCbits = 64;
 constexpr int kBMaxLargeQubits = 24;
 constexpr int kOpChunk = kBThreads * 16 / 64;   // ops staged per chunk: one 16-byte word per thread
 
-enum BOpKind : uint8_t { B_U2 = 0, B_PHASE = 1, B_MULMOD = 2, B_MEASURE = 3 };
+// B_RAW never reaches the device: a 1-target built-in gate that is never diagonal,
+// kept as its id and angles until qk_batch_run forms its matrix (as B_U2).
+enum BOpKind : uint8_t { B_U2 = 0, B_PHASE = 1, B_MULMOD = 2, B_MEASURE = 3, B_RAW = 0x40 };
 
 // One op of a small-circuit program (64 bytes).
 struct BOp {
@@ -65,6 +67,10 @@ struct BOp {
             double u;          // MEASURE uniform
             int32_t dest;      // destination cbit (-1: none)
         } ms;
+        struct {
+            double p[3];       // RAW: the built-in's parameters
+            int32_t id, np;    // its gate id and parameter count
+        } raw;
     };
     uint8_t pad[16];
 };
@@ -411,6 +417,36 @@ bool distinct(const int *q, int k, int n) {
     return true;
 }
 
+// The B_RAW ops of the small circuits as B_U2 (their matrices in FP64, stored as
+// FP32), split over the host's cores for long lists.
+void form_raw_ops(std::vector<qk::BOp> &ops) {
+    const size_t n = ops.size();
+    auto work = [&ops](size_t lo, size_t hi) {
+        for (size_t i = lo; i < hi; ++i) {
+            qk::BOp &op = ops[i];
+            if (op.kind != qk::B_RAW) continue;
+            const double p[3] = {op.raw.p[0], op.raw.p[1], op.raw.p[2]};
+            const int id = op.raw.id, np = op.raw.np;
+            qk::cd m[4];
+            int ntg = 0;
+            qk::builtin_matrix(id, p, np, m, ntg);
+            op.kind = qk::B_U2;
+            for (int e = 0; e < 4; ++e) {
+                op.m[2 * e] = (float)m[e].real();
+                op.m[2 * e + 1] = (float)m[e].imag();
+            }
+        }
+    };
+    const size_t nth = n < (1u << 16) ? 1 : std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (nth == 1) {
+        work(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (size_t t = 0; t < nth; ++t) th.emplace_back(work, n * t / nth, n * (t + 1) / nth);
+    for (auto &t : th) t.join();
+}
+
 // A validated gate of a circuit above 13 qubits (one target, at most one control,
 // no classical condition) as planner ops: a 2x2 op, or one phase op per diagonal
 // entry that is not 1.
@@ -727,11 +763,25 @@ qk_status qk_batch_apply_gate(qk_batch *b, int gate_id, const int *targets, int 
         b->large[b->large_of.back()].gates.push_back(g);
         return QK_OK;
     }
-    qk::cd m[4];
-    qk::builtin_matrix(gate_id, params, np, m, ntg);   // valid: checked above
     qk::BOp op;
     std::memset(&op, 0, sizeof op);
     if (!fill_cond(op, *c, cond_cbits, ncc)) return bfail(b, QK_EINVAL, "batch: bad classical condition");
+    // a gate that is never diagonal (X, Y, H, U3 with theta != 0) is kept as its id
+    // and angles; qk_batch_run forms the matrices on the host's cores
+    if (gate_id == QK_GATE_X || gate_id == QK_GATE_Y || gate_id == QK_GATE_H ||
+        (gate_id == QK_GATE_U3 && params[0] != 0.0)) {
+        op.kind = qk::B_RAW;
+        op.q = (uint8_t)q;
+        op.cmask = cmask;
+        op.raw.id = gate_id;
+        op.raw.np = np;
+        for (int k = 0; k < np; ++k) op.raw.p[k] = params[k];
+        b->ops.push_back(op);
+        c->op_end = (uint32_t)b->ops.size();
+        return QK_OK;
+    }
+    qk::cd m[4];
+    qk::builtin_matrix(gate_id, params, np, m, ntg);   // valid: checked above
     if (m[1] == 0.0 && m[2] == 0.0) {  // diagonal: one phase op per entry that is not 1
         for (int e = 0; e < 2; ++e) {
             const qk::cd f = e ? m[3] : m[0];
@@ -861,6 +911,7 @@ qk_status qk_batch_run(qk_batch *b, int store_states) {
     std::stable_sort(sorted.begin(), sorted.end(), [](const qk::BCirc &x, const qk::BCirc &y) {
         return x.n != y.n ? x.n < y.n : (x.flags & 1u) < (y.flags & 1u);
     });
+    form_raw_ops(b->ops);
     // stage the program in pinned memory so that the copies are truly asynchronous
     const size_t ob = sizeof(qk::BOp) * b->ops.size(), cb = sizeof(qk::BCirc) * sorted.size();
     if (ob + cb > 0 && ob + cb > b->cap_stage) {
